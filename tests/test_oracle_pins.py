@@ -1,0 +1,403 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+None of these checks re-types the oracle's own formulas: each compares the
+oracle with an independent statement (a definition evaluated by brute force,
+an exact solution printed in the paper, a conservation law, a textbook
+special case, or an algebraic identity), chosen so that a dropped term, a
+wrong sign, a wrong index or a transposed matrix in the oracle fails one of
+them.
+"""
+import itertools
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1801_04577_gb300 import inputs as I
+
+EX = np.array(I.EX)
+EY = np.array(I.EY)
+ORDER9 = [(0, 0), (1, 0), (0, 1), (2, 0), (0, 2), (1, 1), (2, 1), (1, 2), (2, 2)]  # Eq. 5
+ORDER5 = [(0, 0), (1, 0), (0, 1), (2, 0), (0, 2)]  # Eq. 14
+
+
+def brute_central(f, ux, uy, order, q):
+    """Eq. 4b / Eq. 13b evaluated as plain sums over the discrete velocities."""
+    return np.array([sum(f[i] * (EX[i] - ux) ** m * (EY[i] - uy) ** n for i in range(q))
+                     for (m, n) in order])
+
+
+def rng_cases(seed, n):
+    r = I.splitmix64_uniform(seed, 14 * n).reshape(n, 14)
+    return r
+
+
+# ---------------------------------------------------------------------------
+# Moment transforms (Sec. 2.1 Eq. 4-6, Sec. 2.2 Eq. 13-17)
+# ---------------------------------------------------------------------------
+def test_central_moments_match_definition_on_4x4_grid():
+    """N(u) M f equals the brute-force central sums of Eq. 4b on a 4x4 grid of
+    random nodes (random f and u): pins every entry of M and N(u)."""
+    r = rng_cases(11, 16)
+    for k in range(16):
+        f = 0.05 + r[k, :9]
+        ux, uy = 0.3 * (2 * r[k, 9] - 1), 0.3 * (2 * r[k, 10] - 1)
+        got = oracle.central_moments(f, ux, uy)
+        want = brute_central(f, ux, uy, ORDER9, 9)
+        np.testing.assert_allclose(got, want, rtol=0, atol=1e-14)
+
+
+def test_thermal_central_moments_match_definition():
+    r = rng_cases(12, 16)
+    for k in range(16):
+        g = 0.05 + r[k, :5]
+        ux, uy = 0.3 * (2 * r[k, 9] - 1), 0.3 * (2 * r[k, 10] - 1)
+        got = oracle.thermal_central_moments(g, ux, uy)
+        want = brute_central(g, ux, uy, ORDER5, 5)
+        np.testing.assert_allclose(got, want, rtol=0, atol=1e-14)
+
+
+def test_round_trip_to_machine_precision():
+    w = I.periodic_box(4, 4)
+    o = oracle.from_workload(w)
+    r = rng_cases(13, 32)
+    for k in range(32):
+        f = 0.05 + r[k, :9]
+        g = 0.05 + r[k, 9:14]
+        ux, uy = 0.2 * (2 * r[k, 0] - 1), 0.2 * (2 * r[k, 1] - 1)
+        kt = oracle.central_moments(f, ux, uy)
+        np.testing.assert_allclose(o.from_central(kt, ux, uy), f, rtol=0, atol=1e-14)
+        kT = oracle.thermal_central_moments(g, ux, uy)
+        np.testing.assert_allclose(o.thermal_from_central(kT, ux, uy), g, rtol=0, atol=1e-14)
+
+
+def test_inverse_shift_is_shift_by_minus_u():
+    """N(-u) N(u) = I and N_T(-u) N_T(u) = I (the moment set is closed under the
+    binomial shift).  The CUDA kernels rely on this to undo the shift."""
+    for ux, uy in [(0.1, -0.07), (0.31, 0.2), (-0.4, 0.05)]:
+        P = oracle.shift_matrix(-ux, -uy) @ oracle.shift_matrix(ux, uy)
+        np.testing.assert_allclose(P, np.eye(9), atol=1e-15)
+        P5 = oracle.thermal_shift_matrix(-ux, -uy) @ oracle.thermal_shift_matrix(ux, uy)
+        np.testing.assert_allclose(P5, np.eye(5), atol=1e-15)
+
+
+def test_numerical_inverses():
+    o = oracle.from_workload(I.periodic_box(4, 4))
+    Minv, MTinv = o.inverse_matrices()
+    np.testing.assert_allclose(Minv @ oracle.moment_matrix(), np.eye(9), atol=1e-15)
+    np.testing.assert_allclose(MTinv @ oracle.thermal_moment_matrix(), np.eye(5), atol=1e-15)
+
+
+# ---------------------------------------------------------------------------
+# Equilibria (Eq. 9, Eq. 19)
+# ---------------------------------------------------------------------------
+def test_rest_equilibrium_is_textbook_weights():
+    """At u = 0 the Eq. 9 equilibrium is the standard D2Q9 weight set
+    (4/9, 1/9, 1/36) and, with c_T^2 = 2/5, every D2Q5 weight is 1/5."""
+    o = oracle.from_workload(I.periodic_box(4, 4))
+    f, g = o.equilibrium(1.0, 0.0, 0.0, 1.0)
+    np.testing.assert_allclose(f * 36, [16, 4, 4, 4, 4, 1, 1, 1, 1], atol=1e-14)
+    np.testing.assert_allclose(g, [0.2] * 5, atol=1e-15)
+
+
+def test_equilibrium_central_moments_are_eq9_eq19():
+    o = oracle.from_workload(I.periodic_box(4, 4))
+    rho, ux, uy, T = 1.03, 0.07, -0.11, 0.6
+    f, g = o.equilibrium(rho, ux, uy, T)
+    cs2 = 1 / 3
+    np.testing.assert_allclose(brute_central(f, ux, uy, ORDER9, 9),
+                               [rho, 0, 0, rho * cs2, rho * cs2, 0, 0, 0, rho * cs2 ** 2],
+                               atol=1e-15)
+    np.testing.assert_allclose(brute_central(g, ux, uy, ORDER5, 5),
+                               [T, 0, 0, 0.4 * T, 0.4 * T], atol=1e-15)
+
+
+def test_equilibrium_is_fixed_point_without_force_or_source():
+    """With F = 0 and Q = 0 the collision leaves an equilibrium unchanged for any
+    rates (Eq. 7 and Eq. 18 only relax towards Eq. 9 / Eq. 19)."""
+    w = I.periodic_box(4, 4, gbeta=0.0, Q=0.0, Fvx=0.0, s_nu=1.7, lambda1=0.6)
+    w.params.s_b = 0.8
+    w.params.s_4 = 1.3
+    o = oracle.from_workload(w)
+    # with gbeta = 0 and no external force, F = 0 whatever T is
+    f, g = o.equilibrium(0.98, -0.05, 0.08, 0.3)
+    # the macros recompute u = (sum f e)/rho, identical to the u above
+    fs, gs, mac = o.collide_node(f, g)
+    np.testing.assert_allclose(fs, f, atol=1e-15)
+    np.testing.assert_allclose(gs, g, atol=1e-15)
+    np.testing.assert_allclose(mac, [0.98, -0.05, 0.08, 0.3], atol=1e-15)
+
+
+def test_forcing_sets_first_central_moments():
+    """With u from Eq. 12 the pre-collision first central moments equal -F/2, and
+    Eq. 7 with Eq. 10 turns them into +F/2 (consistent forcing)."""
+    w = I.periodic_box(4, 4, gbeta=0.02, Fvx=3e-3)
+    o = oracle.from_workload(w)
+    r = rng_cases(21, 1)[0]
+    f = 1 / 9 + 0.02 * (2 * r[:9] - 1)
+    g = 0.1 + 0.05 * r[9:14]
+    fs, gs, mac = o.collide_node(f, g)
+    rho, ux, uy, T = mac
+    Fx = 3e-3
+    Fy = 0.02 * (T - 0.5)
+    pre = brute_central(f, ux, uy, ORDER9, 9)
+    post = brute_central(fs, ux, uy, ORDER9, 9)
+    np.testing.assert_allclose(pre[1:3], [-Fx / 2, -Fy / 2], atol=1e-16)
+    np.testing.assert_allclose(post[1:3], [Fx / 2, Fy / 2], atol=1e-16)
+    np.testing.assert_allclose(post[0], pre[0], atol=1e-15)  # mass conserved
+
+
+def test_relaxation_of_each_central_moment():
+    """Post-collision central moments follow Eq. 7-10 moment by moment: checked
+    with brute-force sums, independently of the oracle's matrices."""
+    w = I.periodic_box(4, 4, gbeta=0.01, Fvx=2e-3, Q=0.0)
+    p = w.params
+    p.s_nu, p.s_b, p.s_3, p.s_4 = 1.6, 1.1, 0.9, 1.2
+    o = oracle.from_workload(w)
+    r = rng_cases(22, 1)[0]
+    f = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4) * (1 + 0.1 * (2 * r[:9] - 1))
+    g = 0.1 + 0.05 * r[9:14]
+    fs, gs, (rho, ux, uy, T) = o.collide_node(f, g)
+    cs2 = 1 / 3
+    Fx, Fy = 2e-3, 0.01 * (T - p.T0)
+    k = brute_central(f, ux, uy, ORDER9, 9)
+    ks = brute_central(fs, ux, uy, ORDER9, 9)
+    sp, sm = (p.s_b + p.s_nu) / 2, (p.s_b - p.s_nu) / 2
+    d20, d02 = k[3] - rho * cs2, k[4] - rho * cs2
+    want = [rho, k[1] + Fx, k[2] + Fy,
+            k[3] - sp * d20 - sm * d02, k[4] - sm * d20 - sp * d02,
+            (1 - p.s_nu) * k[5],
+            (1 - p.s_3) * k[6] + (1 - p.s_3 / 2) * cs2 * Fy,
+            (1 - p.s_3) * k[7] + (1 - p.s_3 / 2) * cs2 * Fx,
+            (1 - p.s_4) * k[8] + p.s_4 * rho * cs2 ** 2]
+    np.testing.assert_allclose(ks, want, atol=1e-15)
+
+
+def test_thermal_relaxation_with_source():
+    """Eq. 23-25 moment by moment, and the zeroth moment becomes T + Q/2 for any
+    lambda0."""
+    for lam0 in (0.5, 1.0, 1.7):
+        w = I.periodic_box(4, 4, Q=3e-3, lambda1=1.2)
+        w.params.lambda0 = lam0
+        w.params.lambda2 = 0.9
+        o = oracle.from_workload(w)
+        r = rng_cases(23, 1)[0]
+        f = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4) * (1 + 0.05 * (2 * r[:9] - 1))
+        g = 0.1 + 0.05 * r[9:14]
+        fs, gs, (rho, ux, uy, T) = o.collide_node(f, g)
+        Q, cT2, l1, l2 = 3e-3, 0.4, 1.2, 0.9
+        assert T == pytest.approx(g.sum() + Q / 2, abs=1e-16)
+        k = brute_central(g, ux, uy, ORDER5, 5)
+        ks = brute_central(gs, ux, uy, ORDER5, 5)
+        want = [T + Q / 2, (1 - l1) * k[1], (1 - l1) * k[2],
+                (1 - l2) * k[3] + l2 * T * cT2 + (1 - l2 / 2) * Q * cT2,
+                (1 - l2) * k[4] + l2 * T * cT2 + (1 - l2 / 2) * Q * cT2]
+        np.testing.assert_allclose(ks, want, atol=1e-15)
+
+
+def test_rate_rules():
+    """s3 non-slip rule (Sec. 3) is TRT's magic parameter 3/16, and the lambda2
+    rule (Sec. 3.1) reproduces the paper's two printed pairs."""
+    for s_nu in (0.6, 1.0, 1.5, 1.9):
+        w = I.periodic_box(4, 4, s_nu=s_nu)
+        s3, _ = oracle.from_workload(w).rates()
+        assert (1 / s_nu - 0.5) * (1 / s3 - 0.5) == pytest.approx(3 / 16, rel=1e-14)
+    for lam1, lam2 in ((4 / 3, 3 / 4), (3 / 4, 4 / 3)):
+        w = I.periodic_box(4, 4, lambda1=lam1)
+        _, l2 = oracle.from_workload(w).rates()
+        assert l2 == pytest.approx(lam2, rel=1e-14)
+
+
+# ---------------------------------------------------------------------------
+# Boundary temperature (Eq. 27-28)
+# ---------------------------------------------------------------------------
+def test_wall_temperature_special_cases():
+    # Dirichlet: b1 = 0, b2 = 1
+    assert oracle.wall_temperature(0, 1, 0.37, 1.0, 0.9, 0.1) == pytest.approx(0.37, abs=1e-16)
+    # Robin/Neumann: exact for any quadratic profile sampled at n.e/2 and 3 n.e/2
+    r = rng_cases(31, 20)
+    for k in range(20):
+        a, b, c = r[k, 0], 2 * r[k, 1] - 1, 2 * r[k, 2] - 1
+        ne = 0.3 + 0.7 * r[k, 3]
+        b1, b2 = 0.2 + r[k, 4], r[k, 5] if k % 2 else 0.0
+        # T(s) with s the distance from the wall into the fluid, n points out of the fluid
+        T = lambda s: a + b * s + c * s * s
+        dTdn = -b
+        b3 = b1 * dTdn + b2 * a
+        Tw = oracle.wall_temperature(b1, b2, b3, ne, T(ne / 2), T(1.5 * ne))
+        assert Tw == pytest.approx(a, abs=1e-13)
+
+
+# ---------------------------------------------------------------------------
+# Conservation on a periodic box
+# ---------------------------------------------------------------------------
+def test_conservation_periodic_box():
+    """No walls: total mass is constant, total momentum grows by the summed
+    force, and sum(g) grows by N Q per step (Eq. 7 conserved rows, Eq. 23)."""
+    w = I.periodic_box(16, 12)
+    p = w.params
+    o = oracle.from_workload(w)
+    n = p.nx * p.ny
+    for _ in range(50):
+        f, g = o.dfs()
+        rho, ux, uy, T = o.moments()
+        m0 = f.sum()
+        px0 = (f * EX).sum()
+        py0 = (f * EY).sum()
+        G0 = g.sum()
+        Fy = p.Fvy + p.rho0 * p.gbeta * (T - p.T0)
+        o.step(1)
+        f1, g1 = o.dfs()
+        assert f1.sum() == pytest.approx(m0, rel=1e-14)
+        assert (f1 * EX).sum() - px0 == pytest.approx(n * p.Fvx, rel=1e-9, abs=1e-15)
+        assert (f1 * EY).sum() - py0 == pytest.approx(Fy.sum(), rel=1e-9, abs=1e-15)
+        assert g1.sum() - G0 == pytest.approx(n * p.Q, rel=1e-9)
+
+
+def test_lambda0_has_no_effect():
+    """The zeroth thermal moment after collision is T + Q/2 whatever lambda0 is,
+    so whole runs agree to rounding."""
+    res = []
+    for lam0 in (0.3, 1.0, 1.9):
+        w = I.obstacle_channel()
+        w.params.lambda0 = lam0
+        o = oracle.from_workload(w)
+        o.step(30)
+        res.append(o.moments())
+    for r in res[1:]:
+        for a, b in zip(r, res[0]):
+            np.testing.assert_allclose(a, b, rtol=0, atol=1e-13)
+
+
+# ---------------------------------------------------------------------------
+# Paper experiments
+# ---------------------------------------------------------------------------
+def _E2(T, Ta):
+    return math.sqrt(((T - Ta) ** 2).sum() / (Ta ** 2).sum())
+
+
+def test_diffusion_with_source_exact(paper_values):
+    """Sec. 3.1: the parabola is reproduced to round-off with the lambda2 rule,
+    at the rates the paper prints for alpha = 1/10 and 1/3."""
+    pv = paper_values["diffusion_with_source"]
+    for case in pv["cases"]:
+        w = I.diffusion_channel(case["alpha"], L=pv["L"])
+        assert w.params.lambda1 == pytest.approx(case["lambda1"], rel=1e-14)
+        o = oracle.from_workload(w)
+        assert o.rates()[1] == pytest.approx(case["lambda2"], rel=1e-14)
+        o.step(6000)
+        T = o.moments()[3]
+        Ta = I.diffusion_exact(pv["L"])
+        for col in range(T.shape[1]):
+            assert _E2(T[:, col], Ta) < 1e-12
+
+
+def test_lambda2_sweep_minimum(paper_values):
+    """Fig. 2: over lambda2 in [0.2, 1.8] the error is smallest at the rule value."""
+    pv = paper_values["diffusion_with_source"]
+    sweep = np.round(np.arange(pv["lambda2_sweep"]["lo"], pv["lambda2_sweep"]["hi"] + 1e-9, 0.1), 10)
+    for case in pv["cases"]:
+        errs = {}
+        for l2 in list(sweep) + [case["lambda2"]]:
+            w = I.diffusion_channel(case["alpha"], lambda2=float(l2), L=pv["L"], nx=1)
+            o = oracle.from_workload(w)
+            o.step(6000)
+            errs[float(l2)] = _E2(o.moments()[3][:, 0], I.diffusion_exact(pv["L"]))
+        best = min(errs, key=errs.get)
+        assert best == pytest.approx(case["lambda2"], abs=1e-12)
+        others = [e for k, e in errs.items() if abs(k - case["lambda2"]) > 1e-9]
+        assert min(others) > 1e3 * errs[best]
+
+
+def test_poiseuille_velocity_with_nonslip_rule():
+    """Velocity part of Sec. 3.2: with the s3 rule, half-way walls sit exactly at
+    the link midpoints and the parabola is exact (round-off with s_b = s_nu)."""
+    ny, nu, Fx = 8, 0.1, 1e-5
+    ua = I.poiseuille_exact(ny, nu, Fx)
+    w = I.poiseuille_channel(ny, nu, Fx)
+    o = oracle.from_workload(w)
+    o.step(8000)
+    ux = o.moments()[1]
+    assert np.abs(ux - ua[:, None]).max() / ua.max() < 1e-10
+    # without the rule (s3 = 1) the wall slips: error is many orders larger
+    w2 = I.poiseuille_channel(ny, nu, Fx)
+    w2.params.s_3 = 1.0
+    o2 = oracle.from_workload(w2)
+    o2.step(8000)
+    assert np.abs(o2.moments()[1] - ua[:, None]).max() / ua.max() > 1e-4
+
+
+def test_conduction_nusselt_is_one():
+    """Pure conduction between Dirichlet walls (no gravity, no source) gives a
+    linear profile, for which Eq. 27 is exact: Nu = +1 at the hot wall and -1
+    at the cold wall."""
+    w = I.natural_convection_cavity(16, 1e4)
+    w.params.gbeta = 0.0
+    w.params.lambda1 = 1.0 / (0.3 / 0.4 + 0.5)
+    o = oracle.from_workload(w)
+    o.step(6000)
+    assert o.nusselt(0, 16, 1.0) == pytest.approx(1.0, abs=1e-10)
+    assert o.nusselt(1, 16, 1.0) == pytest.approx(-1.0, abs=1e-10)
+    assert o.nusselt(2, 16, 1.0) == pytest.approx(0.0, abs=1e-10)  # adiabatic
+
+
+def test_annulus_conduction_closed_form():
+    """Curved walls: steady conduction in the annulus (Dirichlet inside, Robin
+    outside) against T = A + B ln r.  Staircase walls make this first order, so
+    the bound is a grid-study value (about 1% at 64^2)."""
+    n = 64
+    w = I.annulus(n, 2.6, gravity=False, alpha=0.1)
+    o = oracle.from_workload(w)
+    o.step(17000)
+    assert o.residual() < 1e-9
+    T = o.moments()[3]
+    ro = n / 2 - 1
+    ri = ro / 2.6
+    H = ro - ri
+    c = (n - 1) / 2
+    yy, xx = np.mgrid[0:n, 0:n]
+    r = np.hypot(xx - c, yy - c)
+    A, B = np.linalg.solve([[1, math.log(ri)], [1 / H, 1 / ro + math.log(ro) / H]], [1, 0])
+    Ta = A + B * np.log(r)
+    fl = w.geom.solid == 0
+    assert np.abs(T - Ta)[fl].max() < 0.02
+    assert _E2(T[fl], Ta[fl]) < 0.006
+
+
+@pytest.mark.slow
+def test_natural_convection_table1_ra1e3(paper_values):
+    """Sec. 3.3 / Table 1 at Ra = 1e3 on a coarser 48^2 grid: Nu, u_max, v_max
+    within 1% of the paper's CLBM values (the paper used 128^2)."""
+    t1 = paper_values["table1_clbm"]
+    H = 48
+    w = I.natural_convection_cavity(H, 1e3)
+    o = oracle.from_workload(w)
+    o.step(40000)
+    rho, ux, uy, T = o.moments()
+    alpha = (1 / w.params.lambda1 - 0.5) * 0.4
+    Nu_cold = -o.nusselt(1, H, 1.0)
+    um = 0.5 * (ux[:, H // 2 - 1] + ux[:, H // 2]) * H / alpha
+    vm = 0.5 * (uy[H // 2 - 1, :] + uy[H // 2, :]) * H / alpha
+    assert Nu_cold == pytest.approx(t1["Nu"][0], rel=0.01)
+    assert um.max() == pytest.approx(t1["u_max"][0], rel=0.01)
+    assert vm.max() == pytest.approx(t1["v_max"][0], rel=0.01)
+    # hot and cold wall Nusselt numbers agree at steady state
+    assert o.nusselt(0, H, 1.0) == pytest.approx(Nu_cold, rel=1e-3)
+
+
+def test_splitmix_vectorised_matches_definition():
+    ref = I.splitmix64_scalar(I.RB_SEED, 64)
+    vec = I.splitmix64_uniform(I.RB_SEED, 64)
+    np.testing.assert_array_equal(vec, np.array([(z >> 11) for z in ref], dtype=np.float64) / 2.0 ** 53)
+
+
+def test_invalid_descriptions_rejected():
+    w = I.obstacle_channel()
+    # drop one listed link: a fluid->solid D2Q5 link without a condition
+    w.geom.link_node = w.geom.link_node[1:]
+    w.geom.link_dir = w.geom.link_dir[1:]
+    w.geom.link_ne = w.geom.link_ne[1:]
+    w.geom.link_tbc = w.geom.link_tbc[1:]
+    with pytest.raises(ValueError):
+        oracle.from_workload(w)
