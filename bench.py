@@ -1,0 +1,346 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the fused cascaded thermal LBM step on GB300.
+
+Workload (default): Rayleigh-Benard cell 4096 x 2048, periodic in x, bottom
+T = 1, top T = 0, Ra = 1e6, Pr = 0.71, U = 0.1, uniform heat source Q = 1e-5,
+initial T linear plus seeded noise of amplitude 1e-3, FP32 storage and
+collision.  One benchmark step is one lattice time step (one launch of the
+fused collide-and-stream kernel over all nodes).  Metric: MLUPS (million
+fluid-node updates per second), whole job.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+
+Under torchrun with N > 1 every rank advances its own copy of the lattice
+(independent replicas, weak scaling); only the timing is combined (max).
+The reference arm (--impl reference) times the FP64 CPU oracle on the host
+cores on a bounded sample lattice of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1801_04577_gb300 import inputs as I  # noqa: E402
+
+HBM_FALLBACK_GBS = 6800.0
+ELEM_BYTES = {"f64": 8, "f32": 4, "f16": 2, "bf16": 2}
+DTYPE = {"f64": "f64", "f32": "f32", "f16": "f16-storage/f32-compute", "bf16": "bf16-storage/f32-compute"}
+
+# DRAM traffic per launch of the step kernel measured with ncu
+# (dram__bytes_read.sum + dram__bytes_write.sum), keyed by storage type and
+# workload, valid only for the kernel source whose SHA-256 prefix is stored.
+NCU_TRAFFIC = {}
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for name in ("clbm_kernels.cuh", "clbm_internal.h"):
+        with open(os.path.join(ROOT, "paper_1801_04577_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return HBM_FALLBACK_GBS, "fallback"
+
+
+def workload(name: str):
+    if name == "rb4096":
+        return I.rayleigh_benard(4096, 2048)
+    if name == "rb256":
+        return I.rayleigh_benard(256, 128)
+    if name == "rb2048":
+        return I.rayleigh_benard(2048, 1024)
+    if name == "cavity64":
+        return I.natural_convection_cavity(64, 1e4)
+    if name == "annulus2048":
+        return I.annulus(2048, 2.6, Ra=1e5)
+    raise SystemExit(f"unknown workload {name}")
+
+
+def workload_config(w, name, precision):
+    cfg = {"workload": w.name + f"_{precision}", "nx": w.params.nx, "ny": w.params.ny,
+           "fluid_nodes": I.fluid_count(w), "storage": f"{precision} deviations from rest state",
+           "bytes_per_lattice_update": 28 * ELEM_BYTES[precision],
+           "l2": "no flush: inputs larger than L2 (two ping-pong buffers of "
+                 f"{14 * w.params.nx * w.params.ny * ELEM_BYTES[precision] / 1e6:.0f} MB each)"}
+    return cfg
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.idx = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="clocks", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.idx)],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+                except ValueError:
+                    continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for _, _, r in rows for k in range(4) if r[k].lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows),
+                "sm_max_mhz": max(r[1] for r in rows), "reasons": reasons, "samples": len(rows)}
+
+
+def device_index(local_rank: int) -> int:
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis:
+        try:
+            return int(vis.split(",")[local_rank])
+        except (ValueError, IndexError):
+            pass
+    return local_rank
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (reference arm and cpu_baseline)
+# ---------------------------------------------------------------------------
+def oracle_rb_sample(nx: int, ny: int):
+    w = I.rayleigh_benard(nx, ny)
+    import oracle
+    return w, oracle.from_workload(w), oracle.threads()
+
+
+def time_oracle(budget_s: float = 12.0, nx: int = 2048, ny: int = 1024):
+    """MLUPS of the FP64 oracle on an RB sample lattice: steps until the budget."""
+    w, o, cores = oracle_rb_sample(nx, ny)
+    o.step(1)  # warm-up
+    t0 = time.perf_counter()
+    n = 0
+    while True:
+        o.step(1)
+        n += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s or n >= 200:
+            break
+    return {"value": nx * ny * n / el / 1e6, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+            "sample": f"FP64 oracle, Rayleigh-Benard {nx}x{ny} (same parameters as the workload), "
+                      f"{n} steps after 1 warm-up step, {el:.1f} s"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    # size the sample so that warmup + steps finish within about two minutes
+    budget = 120.0
+    w_probe, o_probe, cores = oracle_rb_sample(256, 128)
+    o_probe.step(1)
+    t0 = time.perf_counter()
+    o_probe.step(3)
+    rate = 256 * 128 * 3 / (time.perf_counter() - t0)  # node updates per second
+    total = max(1, args.steps + args.warmup)
+    nodes = max(64 * 32, min(4096 * 2048, int(rate * budget / total)))
+    ny = max(32, int((nodes / 2) ** 0.5))
+    nx = 2 * ny
+    w = I.rayleigh_benard(nx, ny)
+    o = oracle.from_workload(w)
+    o.step(args.warmup)
+    t0 = time.perf_counter()
+    o.step(args.steps)
+    el = time.perf_counter() - t0
+    value = nx * ny * args.steps / el / 1e6
+    line = {"impl": "reference", "metric": "MLUPS", "value": value, "unit": "MLUPS",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": el / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"rayleigh_benard_4096x2048_Ra1e6_{args.precision}",
+                       "sample": f"{nx}x{ny} lattice of the same workload"},
+            "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+                             "sample": f"FP64 oracle, Rayleigh-Benard {nx}x{ny}, {args.steps} steps "
+                                       f"after {args.warmup} warm-up steps"},
+            "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "gpu_launches": 0}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def run_native(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1801_04577_gb300 import clbm
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py: no CUDA device (the library has no CPU path)")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    w = workload(args.workload)
+    p = w.params
+    nodes = I.fluid_count(w)
+    # a dedicated stream: the library launches on it and the events below are
+    # recorded on it (torch's default stream has handle 0, which the library
+    # would replace by a private stream)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    s = clbm.from_workload(w, args.precision, stream=stream.cuda_stream)
+    s.step(args.warmup)
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(device_index(local))
+    sampler.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    clbm.clbm_step(s.ctx, args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    barrier()
+    el_ms = e0.elapsed_time(e1)
+    # the state must still be finite after the timed steps
+    res = s.residual()
+
+    el_t = torch.tensor([el_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(el_t, op=dist.ReduceOp.MAX)
+    el_ms = float(el_t.item())
+    value = world * nodes * args.steps / (el_ms * 1e-3) / 1e6
+
+    # end to end through the public API: host fields in, solve, host fields out
+    e2e = None
+    if not args.no_e2e:
+        n = p.nx * p.ny
+        T_host = torch.from_numpy(w.init.T.astype("float64").ravel()).pin_memory()
+        outs = [torch.empty(n, dtype=torch.float64).pin_memory() for _ in range(3)]
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        clbm.clbm_init_fields(s.ctx, None, None, None, T_host.data_ptr(), on_device=False)
+        clbm.clbm_step(s.ctx, args.steps)
+        clbm.clbm_moments(s.ctx, None, outs[0].data_ptr(), outs[1].data_ptr(), outs[2].data_ptr(),
+                          on_device=False)
+        el2 = time.perf_counter() - t0
+        el2_t = torch.tensor([el2], dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.all_reduce(el2_t, op=dist.ReduceOp.MAX)
+        el2 = float(el2_t.item())
+        e2e = {"value": world * nodes * args.steps / el2 / 1e6, "unit": "MLUPS",
+               "h2d_bytes_per_step": 8 * n / args.steps, "d2h_bytes_per_step": 3 * 8 * n / args.steps,
+               "note": f"per run: one clbm_init_fields from pinned host T ({8 * n} B), "
+                       f"{args.steps} steps, one clbm_moments of ux, uy, T to pinned host "
+                       f"({24 * n} B); bytes reported per lattice step"}
+
+    peak, peak_kind = measured_peak()
+    bytes_lu = 28 * ELEM_BYTES[args.precision]
+    per_launch_s = el_ms * 1e-3 / args.steps
+    achieved = bytes_lu * nodes / per_launch_s / 1e9
+    key = f"{args.precision}:{args.workload}"
+    traffic = None
+    rec = NCU_TRAFFIC.get(key)
+    if rec and rec["kernel_hash"] == kernel_source_hash():
+        traffic = rec["bytes_per_launch"]
+    line = {"metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": el_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": DTYPE[args.precision], "data": "synthetic",
+            "config": dict(workload_config(w, args.workload, args.precision),
+                           parallelism=f"replicas{world}" if world > 1 else "single"),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "kernel": "clbm::step_kernel", "peak_kind": peak_kind,
+                         "algorithmic_bytes_per_launch": bytes_lu * nodes},
+            "gpu_launches": args.steps,
+            "residual_after": res}
+    if e2e is not None:
+        line["e2e"] = e2e
+    if clocks is not None:
+        line["clocks"] = clocks
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = time_oracle()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    s.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20000)
+    ap.add_argument("--warmup", type=int, default=100)
+    ap.add_argument("--impl", choices=["native", "reference"], default="native")
+    ap.add_argument("--precision", choices=list(ELEM_BYTES), default="f32")
+    ap.add_argument("--workload", default="rb4096")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("bench.py: at least 3 warm-up steps are required")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_native(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

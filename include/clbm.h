@@ -1,0 +1,179 @@
+/*
+ * clbm.h - C ABI of the GB300 cascaded thermal lattice Boltzmann library.
+ *
+ * The library advances the double-distribution-function cascaded LBM of
+ * Fei & Luo ("Cascaded lattice Boltzmann method for incompressible thermal
+ * flows with heat sources and general thermal boundary conditions"):
+ * D2Q9 flow distributions f_i (Sec. 2.1, Eq. 3-12) and D2Q5 temperature
+ * distributions g_i (Sec. 2.2, Eq. 13-22), coupled through the Boussinesq
+ * force (Eq. 2), with the central-moment heat source (Sec. 2.3, Eq. 23-25),
+ * half-way bounce-back for velocity (Sec. 3) and the general bounce-back
+ * scheme for Dirichlet / Neumann / Robin temperature walls (Eq. 26-28).
+ *
+ * Conventions
+ *   - Lattice units (dx = dt = 1).  Nodes are cell centres (x+1/2, y+1/2),
+ *     x = 0..nx-1, y = 0..ny-1.  Every array crossing this ABI is row major
+ *     [ny][nx] (x fastest), dense, without padding.
+ *   - D2Q9 directions follow Eq. 3: ex = {0,1,0,-1,0,1,-1,-1,1},
+ *     ey = {0,0,1,0,-1,1,1,-1,-1}; D2Q5 uses directions 0..4.
+ *   - Walls of non-periodic box sides lie half a spacing outside the first
+ *     and last node row/column.  Solid nodes (mask) are walls too.
+ *   - Ownership: the library owns every device allocation it makes; caller
+ *     arrays are only read (inputs) or written (outputs) during the call and
+ *     are never retained.  Host pointers are plain host memory; "device"
+ *     pointers are CUDA device pointers valid on the context's device.
+ *   - Streams: all device work of a context is issued on its stream (the one
+ *     passed to clbm_create, or a stream the library creates for NULL).
+ *     clbm_step only enqueues work; calls that return a host value
+ *     (clbm_moments to host, clbm_nusselt, clbm_residual) synchronise the
+ *     stream before returning.
+ *   - Errors: no call throws or aborts.  Each returns a clbm_status; on a
+ *     failure the context (when there is one) keeps a message readable with
+ *     clbm_last_error().  CLBM_ECUDA means a CUDA runtime call failed.
+ */
+#ifndef CLBM_H_
+#define CLBM_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  CLBM_OK = 0,
+  CLBM_EINVAL = 1,     /* invalid argument or problem description        */
+  CLBM_ENOMEM = 2,     /* device or host allocation failed               */
+  CLBM_ECUDA = 3,      /* a CUDA runtime call or kernel launch failed    */
+  CLBM_EUNSTABLE = 4,  /* NaN or Inf found in the fields                 */
+  CLBM_ETIMEOUT = 5,   /* a bounded device-side wait ran out             */
+  CLBM_ENOTCONV = 6    /* iteration cap reached before convergence       */
+} clbm_status;
+
+/* Storage precision of the distributions.  Every format stores deviations
+ * from the rest state (f_i - w_i rho0, g_i - w^T_i T0, with w the D2Q9
+ * weights 4/9, 1/9, 1/36 and w^T = (1 - 2 cT2, cT2/2 x4)).  The collision is
+ * computed in FP64 for CLBM_F64 and in FP32 for every other format. */
+typedef enum {
+  CLBM_F64 = 0,
+  CLBM_F32 = 1,
+  CLBM_F16DEV = 2,   /* IEEE binary16 deviations, round to nearest even  */
+  CLBM_BF16DEV = 3   /* bfloat16 deviations, round to nearest even       */
+} clbm_precision;
+
+/* Problem parameters (lattice units).
+ *   s_nu  : shear rate, nu = (1/s_nu - 1/2)/3 (Eq. 8 text)
+ *   s_b   : bulk rate, nu_b = (1/s_b - 1/2)/3 (Eq. 8 text)
+ *   s_3   : rate of k~21, k~12; <= 0 selects s3 = (16 - 8 s_nu)/(8 - s_nu) (Sec. 3)
+ *   s_4   : rate of k~22 (Eq. 8)
+ *   lambda0, lambda1, lambda2 : S_T = diag(l0, l1, l1, l2, l2) (Sec. 2.2);
+ *           alpha = (1/lambda1 - 1/2) cT2; lambda2 <= 0 selects
+ *           lambda2 = 12 (lambda1 - 2)/(lambda1 - 12) (Sec. 3.1)
+ *   rho0, T0 : reference density and temperature (Eq. 1-2)
+ *   gbeta : g * beta; the buoyancy force density is rho0 gbeta (T - T0) along +y (Eq. 2)
+ *   Fvx, Fvy : external body force density F_v (Eq. 2)
+ *   Q     : uniform volumetric heat source (Eq. 23-25)
+ *   cT2   : squared D2Q5 sound speed c_T^2 (Eq. 19; 2/5 in Sec. 3) */
+typedef struct {
+  int32_t nx, ny;
+  int32_t periodic_x, periodic_y;
+  int32_t precision; /* clbm_precision */
+  int32_t reserved0;
+  double s_nu, s_b, s_3, s_4;
+  double lambda0, lambda1, lambda2;
+  double rho0, T0, gbeta, Fvx, Fvy, Q, cT2;
+} clbm_params;
+
+/* Thermal wall condition b1 dT/dn + b2 T = b3 (Sec. 2.3), n the unit normal
+ * pointing out of the fluid.  Dirichlet: (0, 1, Tw); Neumann: (1, 0, flux). */
+typedef struct {
+  double b1, b2, b3;
+} clbm_tbc;
+
+/* One wall link of a fluid node into a solid node (Eq. 26-28): the D2Q5 link
+ * `dir` (1..4) leaves fluid node `node` = y*nx + x towards the wall (the e_i
+ * of Eq. 26), `n_dot_e` = n.e_i > 0 of Eq. 27-28, `tbc` indexes the condition
+ * table.  Curved walls are described by such links with the true normal. */
+typedef struct {
+  int32_t node, dir;
+  double n_dot_e;
+  int32_t tbc, reserved;
+} clbm_link;
+
+typedef struct clbm_ctx clbm_ctx;
+
+/* Create a solver for one lattice on the current CUDA device.  Allocates two
+ * distribution buffers (ping-pong) and sets the state to the equilibrium at
+ * rest (rho0, u = 0, T0).  `stream` is a cudaStream_t or NULL.  The lattice
+ * has no walls until clbm_set_boundaries is called (all four box sides must
+ * then be periodic or have a condition).
+ * Errors: CLBM_EINVAL (sizes < 1, non-positive rates, unknown precision),
+ * CLBM_ENOMEM, CLBM_ECUDA. */
+clbm_status clbm_create(const clbm_params* params, void* stream, clbm_ctx** out);
+
+/* Describe the walls (Sec. 2.3, Sec. 3).
+ *   solid    : host uint8 [ny][nx], nonzero = solid node, or NULL (no obstacles)
+ *   tbc      : host table of n_tbc conditions
+ *   side_tbc : host int32[4], condition index of the box sides x0 (left),
+ *              x1 (right), y0 (bottom), y1 (top); ignored on periodic axes
+ *   links    : host array of n_links wall links (may be NULL when n_links = 0);
+ *              every D2Q5 link from a fluid node into a solid node must be listed
+ * All inputs are copied.  The distribution state is left unchanged.
+ * Errors: CLBM_EINVAL for out-of-range indices, a missing link, a fluid node
+ * with no fluid neighbour, or a non-periodic side without a condition. */
+clbm_status clbm_set_boundaries(clbm_ctx* ctx, const uint8_t* solid, const clbm_tbc* tbc,
+                                int32_t n_tbc, const int32_t* side_tbc, const clbm_link* links,
+                                int32_t n_links);
+
+/* Set the state to the equilibrium distributions whose central moments are
+ * Eq. 9 and Eq. 19 at the given fields, i.e. f(t=0) = f^eq(rho, u),
+ * g(t=0) = g^eq(T, u), and reset the step counter.  Each pointer is an FP64
+ * [ny][nx] array or NULL for the rest value (rho0, 0, 0, T0).  on_device
+ * selects device (1) or host (0) pointers. */
+clbm_status clbm_init_fields(clbm_ctx* ctx, const double* rho, const double* ux, const double* uy,
+                             const double* T, int32_t on_device);
+
+/* Enqueue nsteps time steps (collision Eq. 7/23, streaming Eq. 11/21, wall
+ * rules Eq. 26-28) on the context stream.  Returns without synchronising;
+ * CLBM_ECUDA reports a launch failure. */
+clbm_status clbm_step(clbm_ctx* ctx, int64_t nsteps);
+
+/* Macroscopic fields at the current time: rho = sum f (Eq. 12),
+ * u = (sum f e + F/2)/rho (Eq. 12), T = sum g + Q/2 (Eq. 25), as FP64
+ * [ny][nx] arrays; solid nodes report 0.  Any pointer may be NULL.
+ * on_device selects device (1) or host (0) outputs; host outputs synchronise. */
+clbm_status clbm_moments(clbm_ctx* ctx, double* rho, double* ux, double* uy, double* T,
+                         int32_t on_device);
+
+/* Nusselt number of one wall: (length/dT) * mean over its D2Q5 wall links of
+ * dT/dn from Eq. 27 with T_w from Eq. 28, n pointing out of the fluid, so it
+ * is positive where heat enters the fluid.  which = 0..3 selects a box side
+ * (x0, x1, y0, y1); which = 4 + k selects the listed links with condition k.
+ * Accumulated in FP64 in a fixed order (deterministic).  Synchronises.
+ * Errors: CLBM_EINVAL when the selection has no links. */
+clbm_status clbm_nusselt(clbm_ctx* ctx, int32_t which, double length, double dT, double* nu_out);
+
+/* Steady-state residual over the last step: max over phi in {T, ux, uy} of
+ * ||phi(t) - phi(t-1)||_2 / max(||phi(t)||_2, 1e-30) over fluid nodes,
+ * accumulated in FP64 in a fixed order.  Needs at least one step since the
+ * last initialisation (else CLBM_EINVAL).  Returns CLBM_EUNSTABLE (and
+ * r_out = +inf) if any field value is NaN or Inf.  Synchronises. */
+clbm_status clbm_residual(clbm_ctx* ctx, double* r_out);
+
+/* Number of time steps taken since the last initialisation. */
+clbm_status clbm_time(const clbm_ctx* ctx, int64_t* t_out);
+
+/* Free every device and host resource of the context (NULL is allowed). */
+clbm_status clbm_destroy(clbm_ctx* ctx);
+
+/* Message of the last failure on this context ("" if none). */
+const char* clbm_last_error(const clbm_ctx* ctx);
+
+/* Static name of a status code. */
+const char* clbm_status_string(clbm_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CLBM_H_ */

@@ -1,0 +1,255 @@
+"""Thin ctypes binding of libclbm.so (declared in include/clbm.h).
+
+The functions below carry the C names and only marshal arguments: every step
+of the method runs in the library's CUDA kernels.  There is no CPU fallback;
+if the library cannot be loaded, or no CUDA device is present, the calls raise.
+
+Device buffers may be passed as ``torch.Tensor`` (float64, contiguous, on the
+context's device) or as raw integer addresses; host buffers as numpy arrays.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+from . import build as _build
+
+CLBM_OK, CLBM_EINVAL, CLBM_ENOMEM, CLBM_ECUDA, CLBM_EUNSTABLE, CLBM_ETIMEOUT, CLBM_ENOTCONV = range(7)
+CLBM_F64, CLBM_F32, CLBM_F16DEV, CLBM_BF16DEV = range(4)
+PRECISIONS = {"f64": CLBM_F64, "f32": CLBM_F32, "f16": CLBM_F16DEV, "bf16": CLBM_BF16DEV}
+
+
+class clbm_params(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("periodic_x", C.c_int32),
+                ("periodic_y", C.c_int32), ("precision", C.c_int32), ("reserved0", C.c_int32),
+                ("s_nu", C.c_double), ("s_b", C.c_double), ("s_3", C.c_double), ("s_4", C.c_double),
+                ("lambda0", C.c_double), ("lambda1", C.c_double), ("lambda2", C.c_double),
+                ("rho0", C.c_double), ("T0", C.c_double), ("gbeta", C.c_double),
+                ("Fvx", C.c_double), ("Fvy", C.c_double), ("Q", C.c_double), ("cT2", C.c_double)]
+
+
+class clbm_tbc(C.Structure):
+    _fields_ = [("b1", C.c_double), ("b2", C.c_double), ("b3", C.c_double)]
+
+
+class clbm_link(C.Structure):
+    _fields_ = [("node", C.c_int32), ("dir", C.c_int32), ("n_dot_e", C.c_double),
+                ("tbc", C.c_int32), ("reserved", C.c_int32)]
+
+
+EXPORTS = ["clbm_create", "clbm_set_boundaries", "clbm_init_fields", "clbm_step", "clbm_moments",
+           "clbm_nusselt", "clbm_residual", "clbm_time", "clbm_destroy", "clbm_last_error",
+           "clbm_status_string"]
+
+_lib = None
+
+
+class ClbmError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(msg)
+        self.status = status
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(path: Optional[str] = None):
+    """Load libclbm.so (building it first if it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if path is None:
+        path = _build.build()
+    L = C.CDLL(path)
+    vp, dp = C.c_void_p, C.POINTER(C.c_double)
+    L.clbm_create.argtypes = [C.POINTER(clbm_params), vp, C.POINTER(vp)]
+    L.clbm_set_boundaries.argtypes = [vp, vp, C.POINTER(clbm_tbc), C.c_int32, C.POINTER(C.c_int32),
+                                      C.POINTER(clbm_link), C.c_int32]
+    L.clbm_init_fields.argtypes = [vp, vp, vp, vp, vp, C.c_int32]
+    L.clbm_step.argtypes = [vp, C.c_int64]
+    L.clbm_moments.argtypes = [vp, vp, vp, vp, vp, C.c_int32]
+    L.clbm_nusselt.argtypes = [vp, C.c_int32, C.c_double, C.c_double, dp]
+    L.clbm_residual.argtypes = [vp, dp]
+    L.clbm_time.argtypes = [vp, C.POINTER(C.c_int64)]
+    L.clbm_destroy.argtypes = [vp]
+    L.clbm_last_error.argtypes = [vp]
+    L.clbm_last_error.restype = C.c_char_p
+    L.clbm_status_string.argtypes = [C.c_int]
+    L.clbm_status_string.restype = C.c_char_p
+    for name in EXPORTS:
+        if name not in ("clbm_last_error", "clbm_status_string"):
+            getattr(L, name).restype = C.c_int
+    _lib = L
+    return L
+
+
+def _check(st: int, ctx=None, what: str = ""):
+    if st != CLBM_OK:
+        L = load()
+        msg = L.clbm_status_string(st).decode()
+        if ctx is not None:
+            detail = L.clbm_last_error(ctx).decode()
+            if detail:
+                msg += ": " + detail
+        raise ClbmError(st, f"{what}: {msg}" if what else msg)
+
+
+def _addr(a) -> Optional[int]:
+    """Address of a torch tensor, numpy array or raw pointer (None -> NULL)."""
+    if a is None:
+        return None
+    if isinstance(a, int):
+        return a
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("host arrays must be C-contiguous")
+        return a.ctypes.data
+    raise TypeError(f"unsupported buffer type {type(a)}")
+
+
+def make_params(p, precision="f32") -> clbm_params:
+    prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    return clbm_params(p.nx, p.ny, p.periodic_x, p.periodic_y, prec, 0, p.s_nu, p.s_b, p.s_3,
+                       p.s_4, p.lambda0, p.lambda1, p.lambda2, p.rho0, p.T0, p.gbeta, p.Fvx,
+                       p.Fvy, p.Q, p.cT2)
+
+
+# --------------------------------------------------------------------------
+# The C entry points, one Python function each
+# --------------------------------------------------------------------------
+def clbm_create(params: clbm_params, stream: Optional[int] = None) -> C.c_void_p:
+    L = load()
+    ctx = C.c_void_p()
+    _check(L.clbm_create(C.byref(params), stream, C.byref(ctx)), None, "clbm_create")
+    return ctx
+
+
+def clbm_set_boundaries(ctx, solid: Optional[np.ndarray], tbc: Sequence, side_tbc: Sequence[int],
+                        link_node=None, link_dir=None, link_ne=None, link_tbc=None):
+    L = load()
+    n_tbc = len(tbc)
+    tarr = (clbm_tbc * max(n_tbc, 1))(*[clbm_tbc(*map(float, t)) for t in tbc])
+    sides = (C.c_int32 * 4)(*[int(s) for s in side_tbc])
+    n_links = 0 if link_node is None else int(len(link_node))
+    larr = (clbm_link * max(n_links, 1))()
+    for k in range(n_links):
+        larr[k] = clbm_link(int(link_node[k]), int(link_dir[k]), float(link_ne[k]), int(link_tbc[k]), 0)
+    sol = None
+    if solid is not None:
+        sol = np.ascontiguousarray(solid, dtype=np.uint8)
+    _check(L.clbm_set_boundaries(ctx, _addr(sol), tarr, n_tbc, sides, larr, n_links), ctx,
+           "clbm_set_boundaries")
+
+
+def clbm_init_fields(ctx, rho=None, ux=None, uy=None, T=None, on_device: bool = False):
+    L = load()
+    bufs = [rho, ux, uy, T]
+    if not on_device:
+        bufs = [None if b is None else np.ascontiguousarray(b, dtype=np.float64) for b in bufs]
+    _check(L.clbm_init_fields(ctx, *[_addr(b) for b in bufs], int(on_device)), ctx,
+           "clbm_init_fields")
+
+
+def clbm_step(ctx, nsteps: int):
+    _check(load().clbm_step(ctx, int(nsteps)), ctx, "clbm_step")
+
+
+def clbm_moments(ctx, rho=None, ux=None, uy=None, T=None, on_device: bool = False):
+    _check(load().clbm_moments(ctx, *[_addr(b) for b in (rho, ux, uy, T)], int(on_device)), ctx,
+           "clbm_moments")
+
+
+def clbm_nusselt(ctx, which: int, length: float, dT: float) -> float:
+    out = C.c_double()
+    _check(load().clbm_nusselt(ctx, int(which), float(length), float(dT), C.byref(out)), ctx,
+           "clbm_nusselt")
+    return out.value
+
+
+def clbm_residual(ctx) -> float:
+    out = C.c_double()
+    _check(load().clbm_residual(ctx, C.byref(out)), ctx, "clbm_residual")
+    return out.value
+
+
+def clbm_time(ctx) -> int:
+    out = C.c_int64()
+    _check(load().clbm_time(ctx, C.byref(out)), ctx, "clbm_time")
+    return out.value
+
+
+def clbm_destroy(ctx):
+    if ctx is not None and ctx.value:
+        load().clbm_destroy(ctx)
+
+
+def clbm_last_error(ctx) -> str:
+    return load().clbm_last_error(ctx).decode()
+
+
+# --------------------------------------------------------------------------
+# Convenience wrapper around one context
+# --------------------------------------------------------------------------
+class Solver:
+    """One lattice on the GPU, described by ``inputs.Params`` / ``inputs.Geometry``."""
+
+    def __init__(self, params, geom=None, precision="f32", stream: Optional[int] = None, init=None):
+        self.params = params
+        self.nx, self.ny = params.nx, params.ny
+        self.precision = precision
+        self.ctx = clbm_create(make_params(params, precision), stream)
+        if geom is not None:
+            clbm_set_boundaries(self.ctx, geom.solid, geom.tbc, geom.side_tbc, geom.link_node,
+                                geom.link_dir, geom.link_ne, geom.link_tbc)
+        if init is not None:
+            self.init(init)
+
+    def close(self):
+        if getattr(self, "ctx", None) is not None:
+            clbm_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def init(self, fields=None):
+        shape = (self.ny, self.nx)
+        if fields is None:
+            clbm_init_fields(self.ctx)
+            return
+        arrs = []
+        for a in (fields.rho, fields.ux, fields.uy, fields.T):
+            arrs.append(None if a is None else np.ascontiguousarray(np.broadcast_to(a, shape), np.float64))
+        clbm_init_fields(self.ctx, *arrs)
+
+    def step(self, n: int = 1):
+        clbm_step(self.ctx, n)
+
+    def moments(self):
+        shape = (self.ny, self.nx)
+        out = [np.empty(shape) for _ in range(4)]
+        clbm_moments(self.ctx, *out)
+        return tuple(out)
+
+    def nusselt(self, which: int, length: float, dT: float) -> float:
+        return clbm_nusselt(self.ctx, which, length, dT)
+
+    def residual(self) -> float:
+        return clbm_residual(self.ctx)
+
+    @property
+    def time(self) -> int:
+        return clbm_time(self.ctx)
+
+
+def from_workload(w, precision="f32", stream=None) -> Solver:
+    return Solver(w.params, w.geom, precision, stream, w.init)

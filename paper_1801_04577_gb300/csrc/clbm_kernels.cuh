@@ -1,0 +1,733 @@
+// Device code of the fused cascaded thermal LBM step for sm_103a.
+//
+// One time step per node, in one pass over HBM (pull scheme):
+//   pull      f_i(x) = f*_i(x - e_i), g_i(x) = g*_i(x - e_i)      Eq. 11, Eq. 21
+//   walls     half-way bounce-back for f (Sec. 3); general bounce-back for g
+//             with T_w from Eq. 28                                  Eq. 26-28
+//   macros    T = sum g + Q/2, F = F_v + rho0 g beta (T - T0) e_y,
+//             rho = sum f, u = (sum f e + F/2)/rho                 Eq. 25, 2, 12
+//   collide   central moments (Eq. 4-6), relaxation (Eq. 7-10),
+//             back-transformation (text after Eq. 11)
+//   thermal   Eq. 15-20 with the heat source of Eq. 23-24
+//   store     f*(x), g*(x)
+//
+// Layout and precision.  The state kept in HBM is the post-collision pair
+// (f*, g*) at time t, stored structure-of-arrays as deviations from the rest
+// state, d_i = f*_i - w_i rho0 and h_i = g*_i - w^T_i T0.  The collision is
+// rewritten in these deviations (the rest-state moments at velocity u are
+// known in closed form), so every intermediate is a small number and FP32
+// keeps its relative precision on the physically relevant part.
+//
+// Moment transforms.  The nine moments {0,1,2}^2 of Eq. 5 are a tensor
+// product, so N(u) M f is computed as a 1-D central-moment transform along x
+// for each of the three rows of velocities, then along y (and the inverse in
+// the opposite order).  This is the same linear map as Eq. 6, evaluated with
+// about a quarter of the operations; it relies on N(u)^-1 = N(-u).
+//
+// Vectorisation.  A warp owns 32*V consecutive nodes of one row; each lane
+// loads V contiguous values of every plane with one 16-byte (8-byte for
+// 16-bit storage) load.  The x-shift of the pull is done with one warp
+// shuffle per plane; lanes 0 and 31 fetch the single value that crosses the
+// warp boundary.  Nodes on box edges and next to solids take a fix-up path.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "clbm_internal.h"
+
+namespace clbm {
+
+constexpr int kStepThreads = 128;
+
+// ---------------------------------------------------------------------------
+// Lattice (Eq. 3)
+// ---------------------------------------------------------------------------
+__host__ __device__ constexpr int ex_of(int d) {
+  return (d == 1 || d == 5 || d == 8) ? 1 : ((d == 3 || d == 6 || d == 7) ? -1 : 0);
+}
+__host__ __device__ constexpr int ey_of(int d) {
+  return (d == 2 || d == 5 || d == 6) ? 1 : ((d == 4 || d == 7 || d == 8) ? -1 : 0);
+}
+__host__ __device__ constexpr int opp_of(int d) {
+  return d == 0 ? 0 : (d <= 4 ? ((d + 1) % 4) + 1 : ((d - 5 + 2) % 4) + 5);
+}
+// box side crossed by the pull source of D2Q5 direction j: 1 -> x0, 2 -> y0, 3 -> x1, 4 -> y1
+__host__ __device__ constexpr int side_of(int j) {
+  return j == 1 ? 0 : (j == 2 ? 2 : (j == 3 ? 1 : 3));
+}
+
+// ---------------------------------------------------------------------------
+// Storage formats
+// ---------------------------------------------------------------------------
+template <typename S>
+struct Traits;
+template <>
+struct Traits<double> {
+  using R = double;
+  static constexpr int V = 2;
+};
+template <>
+struct Traits<float> {
+  using R = float;
+  static constexpr int V = 4;
+};
+template <>
+struct Traits<__half> {
+  using R = float;
+  static constexpr int V = 4;
+};
+template <>
+struct Traits<__nv_bfloat16> {
+  using R = float;
+  static constexpr int V = 4;
+};
+
+__device__ __forceinline__ double to_r(double v) { return v; }
+__device__ __forceinline__ float to_r(float v) { return v; }
+__device__ __forceinline__ float to_r(__half v) { return __half2float(v); }
+__device__ __forceinline__ float to_r(__nv_bfloat16 v) { return __bfloat162float(v); }
+
+template <typename S, typename R>
+__device__ __forceinline__ S from_r(R v);
+template <>
+__device__ __forceinline__ double from_r<double, double>(double v) { return v; }
+template <>
+__device__ __forceinline__ float from_r<float, float>(float v) { return v; }
+template <>
+__device__ __forceinline__ __half from_r<__half, float>(float v) { return __float2half_rn(v); }
+template <>
+__device__ __forceinline__ __nv_bfloat16 from_r<__nv_bfloat16, float>(float v) {
+  return __float2bfloat16_rn(v);
+}
+
+// Vector load / store of V consecutive elements (16-byte or 8-byte aligned).
+__device__ __forceinline__ void ldv(const double* p, double (&o)[2]) {
+  const double2 v = *reinterpret_cast<const double2*>(p);
+  o[0] = v.x;
+  o[1] = v.y;
+}
+__device__ __forceinline__ void ldv(const float* p, float (&o)[4]) {
+  const float4 v = *reinterpret_cast<const float4*>(p);
+  o[0] = v.x;
+  o[1] = v.y;
+  o[2] = v.z;
+  o[3] = v.w;
+}
+__device__ __forceinline__ void ldv(const __half* p, float (&o)[4]) {
+  const uint2 raw = *reinterpret_cast<const uint2*>(p);
+  __half2 a, b;
+  memcpy(&a, &raw.x, 4);
+  memcpy(&b, &raw.y, 4);
+  const float2 fa = __half22float2(a), fb = __half22float2(b);
+  o[0] = fa.x;
+  o[1] = fa.y;
+  o[2] = fb.x;
+  o[3] = fb.y;
+}
+__device__ __forceinline__ void ldv(const __nv_bfloat16* p, float (&o)[4]) {
+  const uint2 raw = *reinterpret_cast<const uint2*>(p);
+  __nv_bfloat162 a, b;
+  memcpy(&a, &raw.x, 4);
+  memcpy(&b, &raw.y, 4);
+  const float2 fa = __bfloat1622float2(a), fb = __bfloat1622float2(b);
+  o[0] = fa.x;
+  o[1] = fa.y;
+  o[2] = fb.x;
+  o[3] = fb.y;
+}
+
+__device__ __forceinline__ void stv(double* p, const double (&o)[2]) {
+  *reinterpret_cast<double2*>(p) = make_double2(o[0], o[1]);
+}
+__device__ __forceinline__ void stv(float* p, const float (&o)[4]) {
+  *reinterpret_cast<float4*>(p) = make_float4(o[0], o[1], o[2], o[3]);
+}
+__device__ __forceinline__ void stv(__half* p, const float (&o)[4]) {
+  const __half2 a = __floats2half2_rn(o[0], o[1]), b = __floats2half2_rn(o[2], o[3]);
+  uint2 raw;
+  memcpy(&raw.x, &a, 4);
+  memcpy(&raw.y, &b, 4);
+  *reinterpret_cast<uint2*>(p) = raw;
+}
+__device__ __forceinline__ void stv(__nv_bfloat16* p, const float (&o)[4]) {
+  const __nv_bfloat162 a = __floats2bfloat162_rn(o[0], o[1]), b = __floats2bfloat162_rn(o[2], o[3]);
+  uint2 raw;
+  memcpy(&raw.x, &a, 4);
+  memcpy(&raw.y, &b, 4);
+  *reinterpret_cast<uint2*>(p) = raw;
+}
+
+// ---------------------------------------------------------------------------
+// Constants in the compute type
+// ---------------------------------------------------------------------------
+template <typename R>
+struct Co {
+  R rho0, T0, s_nu, s_b, s3, s4, l1, l2;
+  R rgb;   // rho0 * g beta
+  R Fvx, Fvy, Q, hQ, cT2;
+};
+
+template <typename R>
+__host__ __device__ __forceinline__ Co<R> make_co(const DevCoef& c) {
+  Co<R> o;
+  o.rho0 = (R)c.rho0;
+  o.T0 = (R)c.T0;
+  o.s_nu = (R)c.s_nu;
+  o.s_b = (R)c.s_b;
+  o.s3 = (R)c.s3;
+  o.s4 = (R)c.s4;
+  o.l1 = (R)c.l1;
+  o.l2 = (R)c.l2;
+  o.rgb = (R)(c.rho0 * c.gbeta);
+  o.Fvx = (R)c.Fvx;
+  o.Fvy = (R)c.Fvy;
+  o.Q = (R)c.Q;
+  o.hQ = (R)(0.5 * c.Q);
+  o.cT2 = (R)c.cT2;
+  return o;
+}
+
+// ---------------------------------------------------------------------------
+// 1-D central-moment transform over the velocities {-1, 0, +1} and back
+// ---------------------------------------------------------------------------
+template <typename R>
+__host__ __device__ __forceinline__ void fwd1(R am, R a0, R ap, R u, R& c0, R& c1, R& c2) {
+  c0 = am + a0 + ap;
+  const R s = ap - am;
+  c1 = s - u * c0;
+  c2 = (ap + am) - (u + u) * s + u * u * c0;
+}
+template <typename R>
+__host__ __device__ __forceinline__ void inv1(R c0, R c1, R c2, R u, R& am, R& a0, R& ap) {
+  const R r1 = c1 + u * c0;
+  const R r2 = c2 + (u + u) * c1 + u * u * c0;
+  a0 = c0 - r2;
+  ap = R(0.5) * (r2 + r1);
+  am = R(0.5) * (r2 - r1);
+}
+
+// ---------------------------------------------------------------------------
+// Collision of one node, on deviations.  In: pre-collision deviations d, h.
+// Out (in place): post-collision deviations.
+// ---------------------------------------------------------------------------
+template <typename R>
+__host__ __device__ __forceinline__ void collide(const Co<R>& c, R (&d)[9], R (&h)[5]) {
+  const R third = R(1.0 / 3.0);
+  // Eq. 25 (T - T0 = sum h + Q/2) and Eq. 2
+  const R sh = (h[0] + h[1]) + (h[2] + h[3]) + h[4];
+  const R dT = sh + c.hQ;
+  const R Fx = c.Fvx;
+  const R Fy = c.Fvy + c.rgb * dT;
+  // Eq. 12 (sum_i w_i e_i = 0, so the rest state adds nothing to j)
+  const R drho = ((d[0] + d[1]) + (d[2] + d[3])) + ((d[4] + d[5]) + (d[6] + d[7])) + d[8];
+  const R rho = c.rho0 + drho;
+  const R jx = (d[1] - d[3]) + (d[5] - d[6]) + (d[8] - d[7]);
+  const R jy = (d[2] - d[4]) + (d[5] - d[7]) + (d[6] - d[8]);
+  const R inv_rho = R(1) / rho;
+  const R ux = (jx + R(0.5) * Fx) * inv_rho;
+  const R uy = (jy + R(0.5) * Fy) * inv_rho;
+
+  // central moments of the deviations: x-pass per velocity row, then y-pass
+  R xm0, xm1, xm2, xz0, xz1, xz2, xp0, xp1, xp2;
+  fwd1(d[7], d[4], d[8], ux, xm0, xm1, xm2);  // e_y = -1
+  fwd1(d[3], d[0], d[1], ux, xz0, xz1, xz2);  // e_y =  0
+  fwd1(d[6], d[2], d[5], ux, xp0, xp1, xp2);  // e_y = +1
+  R b00, b01, b02, b10, b11, b12, b20, b21, b22;
+  fwd1(xm0, xz0, xp0, uy, b00, b01, b02);
+  fwd1(xm1, xz1, xp1, uy, b10, b11, b12);
+  fwd1(xm2, xz2, xp2, uy, b20, b21, b22);
+
+  // Eq. 7-10, minus the rest-state moments rho0 kappa_m(ux) kappa_n(uy),
+  // kappa = (1, -u, 1/3 + u^2)
+  const R ux2 = ux * ux, uy2 = uy * uy;
+  const R r0 = c.rho0;
+  const R D00 = b00;
+  const R D10 = b10 + Fx;
+  const R D01 = b01 + Fy;
+  const R a20 = r0 * ux2 + b20 - third * drho;
+  const R a02 = r0 * uy2 + b02 - third * drho;
+  const R sum = (R(1) - c.s_b) * (a20 + a02);
+  const R dif = (R(1) - c.s_nu) * (a20 - a02);
+  const R D20 = third * drho - r0 * ux2 + R(0.5) * (sum + dif);
+  const R D02 = third * drho - r0 * uy2 + R(0.5) * (sum - dif);
+  const R D11 = (R(1) - c.s_nu) * b11 - c.s_nu * r0 * ux * uy;
+  const R hs3 = (R(1) - R(0.5) * c.s3) * third;
+  const R D21 = (R(1) - c.s3) * b21 + c.s3 * r0 * (third + ux2) * uy + hs3 * Fy;
+  const R D12 = (R(1) - c.s3) * b12 + c.s3 * r0 * ux * (third + uy2) + hs3 * Fx;
+  const R D22 = (R(1) - c.s4) * b22 - c.s4 * r0 * (third * (ux2 + uy2) + ux2 * uy2) +
+                c.s4 * R(1.0 / 9.0) * drho;
+
+  // back-transformation: y-pass inverse per x-order, then x-pass inverse per row
+  R ym0, yz0, yp0, ym1, yz1, yp1, ym2, yz2, yp2;
+  inv1(D00, D01, D02, uy, ym0, yz0, yp0);
+  inv1(D10, D11, D12, uy, ym1, yz1, yp1);
+  inv1(D20, D21, D22, uy, ym2, yz2, yp2);
+  inv1(ym0, ym1, ym2, ux, d[7], d[4], d[8]);
+  inv1(yz0, yz1, yz2, ux, d[3], d[0], d[1]);
+  inv1(yp0, yp1, yp2, ux, d[6], d[2], d[5]);
+
+  // thermal (Eq. 15-20, 23-24) on deviations from w^T T0; kappa^T = (1, -u, cT2 + u^2)
+  const R k10 = h[1] - h[3], k01 = h[2] - h[4];
+  const R k20 = h[1] + h[3], k02 = h[2] + h[4];
+  const R t10 = k10 - ux * sh;
+  const R t01 = k01 - uy * sh;
+  const R t20 = k20 - (ux + ux) * k10 + ux2 * sh;
+  const R t02 = k02 - (uy + uy) * k01 + uy2 * sh;
+  const R T0 = c.T0;
+  const R E00 = sh + c.Q;
+  const R E10 = (R(1) - c.l1) * t10 + c.l1 * T0 * ux;
+  const R E01 = (R(1) - c.l1) * t01 + c.l1 * T0 * uy;
+  const R src2 = (R(1) - R(0.5) * c.l2) * c.Q * c.cT2 + c.l2 * c.cT2 * dT;
+  const R E20 = (R(1) - c.l2) * t20 - c.l2 * T0 * ux2 + src2;
+  const R E02 = (R(1) - c.l2) * t02 - c.l2 * T0 * uy2 + src2;
+  const R q10 = E10 + ux * E00, q01 = E01 + uy * E00;
+  const R q20 = E20 + (ux + ux) * E10 + ux2 * E00;
+  const R q02 = E02 + (uy + uy) * E01 + uy2 * E00;
+  h[0] = E00 - q20 - q02;
+  h[1] = R(0.5) * (q20 + q10);
+  h[3] = R(0.5) * (q20 - q10);
+  h[2] = R(0.5) * (q02 + q01);
+  h[4] = R(0.5) * (q02 - q01);
+}
+
+// Pre-collision equilibrium deviations (central moments Eq. 9 and Eq. 19 minus
+// the rest-state moments) at (rho, u, T).
+template <typename R>
+__host__ __device__ __forceinline__ void equilibrium(const Co<R>& c, R rho, R ux, R uy, R T, R (&d)[9],
+                                            R (&h)[5]) {
+  const R third = R(1.0 / 3.0);
+  const R r0 = c.rho0, drho = rho - r0, ux2 = ux * ux, uy2 = uy * uy;
+  const R E00 = drho, E10 = r0 * ux, E01 = r0 * uy;
+  const R E20 = third * drho - r0 * ux2, E02 = third * drho - r0 * uy2;
+  const R E11 = -r0 * ux * uy;
+  const R E21 = r0 * (third + ux2) * uy, E12 = r0 * ux * (third + uy2);
+  const R E22 = R(1.0 / 9.0) * drho - r0 * (third * (ux2 + uy2) + ux2 * uy2);
+  R ym0, yz0, yp0, ym1, yz1, yp1, ym2, yz2, yp2;
+  inv1(E00, E01, E02, uy, ym0, yz0, yp0);
+  inv1(E10, E11, E12, uy, ym1, yz1, yp1);
+  inv1(E20, E21, E22, uy, ym2, yz2, yp2);
+  inv1(ym0, ym1, ym2, ux, d[7], d[4], d[8]);
+  inv1(yz0, yz1, yz2, ux, d[3], d[0], d[1]);
+  inv1(yp0, yp1, yp2, ux, d[6], d[2], d[5]);
+  const R dT = T - c.T0;
+  const R T0 = c.T0;
+  const R e00 = dT, e10 = T0 * ux, e01 = T0 * uy;
+  const R e20 = c.cT2 * dT - T0 * ux2, e02 = c.cT2 * dT - T0 * uy2;
+  const R q10 = e10 + ux * e00, q01 = e01 + uy * e00;
+  const R q20 = e20 + (ux + ux) * e10 + ux2 * e00;
+  const R q02 = e02 + (uy + uy) * e01 + uy2 * e00;
+  h[0] = e00 - q20 - q02;
+  h[1] = R(0.5) * (q20 + q10);
+  h[3] = R(0.5) * (q20 - q10);
+  h[2] = R(0.5) * (q02 + q01);
+  h[4] = R(0.5) * (q02 - q01);
+}
+
+// ---------------------------------------------------------------------------
+// Wall temperature (Eq. 28), one-sided when the second node is missing
+// ---------------------------------------------------------------------------
+template <typename R>
+__host__ __device__ __forceinline__ R wall_temperature(R b1, R b2, R b3, R ne, R T1, R T2, bool have2) {
+  if (have2) return (R(9) * b1 * T1 - b1 * T2 + R(3) * ne * b3) / (R(8) * b1 + R(3) * ne * b2);
+  return (R(2) * b1 * T1 + ne * b3) / (R(2) * b1 + ne * b2);
+}
+
+// T at a node from its post-collision thermal deviations: T = T0 + sum h* - Q/2.
+template <typename S, typename R>
+__device__ __forceinline__ R node_T(const S* __restrict__ src, long long plane, long long idx,
+                                    const Co<R>& c) {
+  R s = to_r(src[9 * plane + idx]);
+#pragma unroll
+  for (int q = 10; q < 14; ++q) s += to_r(src[q * plane + idx]);
+  return c.T0 + s - c.hQ;
+}
+
+// Fix-up of one node that touches a wall, a periodic seam or a solid.
+template <typename S, bool MASK, typename R>
+__device__ __forceinline__ void fixup(const StepArgs& a, const Co<R>& c, const S* __restrict__ src,
+                                      int x, int y, uint16_t fl, R (&d)[9], R (&h)[5]) {
+  const DevGeom& g = a.g;
+  const long long plane = g.plane;
+  const long long own = (long long)y * g.pitch + x;
+  const R T1 = node_T(src, plane, own, c);
+#pragma unroll
+  for (int j = 1; j < 9; ++j) {
+    const int ex = ex_of(j), ey = ey_of(j);
+    int sx = x - ex, sy = y - ey;
+    const bool outx = sx < 0 || sx >= g.nx;
+    const bool outy = sy < 0 || sy >= g.ny;
+    const bool boxwall = (outx && !g.px) || (outy && !g.py);
+    bool wall = boxwall;
+    if (MASK) wall = wall || ((fl >> (j - 1)) & 1u);
+    if (wall) {
+      const int i = opp_of(j);
+      d[j] = to_r(src[i * plane + own]);  // half-way bounce-back
+      if (j <= 4) {
+        R ne, b1, b2, b3;
+        if (boxwall) {
+          const int sd = side_of(j);
+          ne = R(1);
+          b1 = (R)g.side_b[sd][0];
+          b2 = (R)g.side_b[sd][1];
+          b3 = (R)g.side_b[sd][2];
+        } else {
+          const int s = g.slot[own];
+          const int t = g.lk_tbc[4 * s + (i - 1)];
+          ne = (R)g.lk_ne[4 * s + (i - 1)];
+          b1 = (R)g.tbc[3 * t + 0];
+          b2 = (R)g.tbc[3 * t + 1];
+          b3 = (R)g.tbc[3 * t + 2];
+        }
+        // second node x_f - e_i = x + e_j, away from the wall
+        int x2 = x + ex, y2 = y + ey;
+        bool have2 = true;
+        if (x2 < 0 || x2 >= g.nx) {
+          if (g.px)
+            x2 = x2 < 0 ? x2 + g.nx : x2 - g.nx;
+          else
+            have2 = false;
+        }
+        if (y2 < 0 || y2 >= g.ny) {
+          if (g.py)
+            y2 = y2 < 0 ? y2 + g.ny : y2 - g.ny;
+          else
+            have2 = false;
+        }
+        const long long i2 = (long long)y2 * g.pitch + x2;
+        if (MASK && have2) have2 = (g.flags[i2] & kFlagSolid) == 0;
+        const R T2 = have2 ? node_T(src, plane, i2, c) : R(0);
+        const R Tw = wall_temperature(b1, b2, b3, ne, T1, T2, have2);
+        h[j] = -to_r(src[(9 + i) * plane + own]) + c.cT2 * (Tw - c.T0);  // Eq. 26
+      }
+    } else if (outx || outy) {  // periodic seam
+      if (outx) sx = sx < 0 ? sx + g.nx : sx - g.nx;
+      if (outy) sy = sy < 0 ? sy + g.ny : sy - g.ny;
+      const long long s = (long long)sy * g.pitch + sx;
+      d[j] = to_r(src[j * plane + s]);
+      if (j <= 4) h[j] = to_r(src[(9 + j) * plane + s]);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// The fused step kernel
+// ---------------------------------------------------------------------------
+template <typename S, bool MASK>
+__global__ void __launch_bounds__(kStepThreads) step_kernel(const StepArgs a) {
+  using R = typename Traits<S>::R;
+  constexpr int V = Traits<S>::V;
+  const DevGeom& g = a.g;
+  const int lane = threadIdx.x & 31;
+  const int warp = blockIdx.x * (kStepThreads / 32) + (threadIdx.x >> 5);
+  const int xw = warp * 32 * V;
+  if (xw >= g.nx) return;  // whole warps only: shuffles below need all 32 lanes
+  const int y = blockIdx.y;
+  const int x0 = xw + lane * V;
+  const long long plane = g.plane;
+  const S* __restrict__ src = static_cast<const S*>(a.src);
+  S* __restrict__ dst = static_cast<S*>(a.dst);
+  const Co<R> c = make_co<R>(a.c);
+
+  int ym = y - 1, yp = y + 1;  // rows the e_y = +1 / -1 populations come from
+  if (g.py) {
+    ym = ym < 0 ? g.ny - 1 : ym;
+    yp = yp >= g.ny ? 0 : yp;
+  } else {  // clamped rows are never used: the fix-up replaces those values
+    ym = ym < 0 ? 0 : ym;
+    yp = yp >= g.ny ? g.ny - 1 : yp;
+  }
+  const int xl = x0 > 0 ? x0 - 1 : 0;
+  const int xr = x0 + V < g.pitch ? x0 + V : g.pitch - 1;
+
+  R v[14][V];
+#pragma unroll
+  for (int q = 0; q < 14; ++q) {
+    const int dir = q < 9 ? q : q - 9;
+    const int ex = ex_of(dir), ey = ey_of(dir);
+    const int row = ey > 0 ? ym : (ey < 0 ? yp : y);
+    const S* base = src + q * plane + (long long)row * g.pitch;
+    R t[V];
+    ldv(base + x0, t);
+    if (ex == 0) {
+#pragma unroll
+      for (int k = 0; k < V; ++k) v[q][k] = t[k];
+    } else if (ex > 0) {  // value from x - 1
+      R left = __shfl_up_sync(0xffffffffu, t[V - 1], 1);
+      if (lane == 0) left = to_r(base[xl]);
+      v[q][0] = left;
+#pragma unroll
+      for (int k = 1; k < V; ++k) v[q][k] = t[k - 1];
+    } else {  // value from x + 1
+      R right = __shfl_down_sync(0xffffffffu, t[0], 1);
+      if (lane == 31) right = to_r(base[xr]);
+#pragma unroll
+      for (int k = 0; k < V - 1; ++k) v[q][k] = t[k + 1];
+      v[q][V - 1] = right;
+    }
+  }
+
+  uint16_t fl[V];
+#pragma unroll
+  for (int k = 0; k < V; ++k) fl[k] = 0;
+  if (MASK) {
+    const uint16_t* fp = g.flags + (long long)y * g.pitch + x0;
+#pragma unroll
+    for (int k = 0; k < V; ++k) fl[k] = fp[k];
+  }
+  const bool yedge = !g.py && (y == 0 || y == g.ny - 1);
+
+#pragma unroll
+  for (int k = 0; k < V; ++k) {
+    const int x = x0 + k;
+    R d[9], h[5];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) d[q] = v[q][k];
+#pragma unroll
+    for (int q = 0; q < 5; ++q) h[q] = v[9 + q][k];
+    bool active = x < g.nx;
+    if (MASK) active = active && !(fl[k] & kFlagSolid);
+    bool edge = yedge || x == 0 || x == g.nx - 1;
+    if (MASK) edge = edge || (fl[k] & 0xFFu);
+    if (active && edge) fixup<S, MASK>(a, c, src, x, y, fl[k], d, h);
+    collide(c, d, h);
+    if (!active) {
+#pragma unroll
+      for (int q = 0; q < 9; ++q) d[q] = R(0);
+#pragma unroll
+      for (int q = 0; q < 5; ++q) h[q] = R(0);
+    }
+#pragma unroll
+    for (int q = 0; q < 9; ++q) v[q][k] = d[q];
+#pragma unroll
+    for (int q = 0; q < 5; ++q) v[9 + q][k] = h[q];
+  }
+
+#pragma unroll
+  for (int q = 0; q < 14; ++q) stv(dst + q * plane + (long long)y * g.pitch + x0, v[q]);
+}
+
+// ---------------------------------------------------------------------------
+// Initialisation: equilibrium at the given fields, then one collision (the
+// stored state is post-collision).
+// ---------------------------------------------------------------------------
+template <typename S>
+__global__ void init_kernel(const DevGeom g, const DevCoef cf, S* __restrict__ dst,
+                            const double* __restrict__ rho, const double* __restrict__ ux,
+                            const double* __restrict__ uy, const double* __restrict__ T) {
+  using R = typename Traits<S>::R;
+  const Co<R> c = make_co<R>(cf);
+  const long long n = (long long)g.ny * g.pitch;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int y = (int)(i / g.pitch), x = (int)(i - (long long)y * g.pitch);
+    R d[9], h[5];
+    bool active = x < g.nx;
+    if (g.flags) active = active && !(g.flags[i] & kFlagSolid);
+    if (active) {
+      const long long k = (long long)y * g.nx + x;
+      const R r = rho ? (R)rho[k] : c.rho0;
+      const R u = ux ? (R)ux[k] : R(0);
+      const R w = uy ? (R)uy[k] : R(0);
+      const R t = T ? (R)T[k] : c.T0;
+      equilibrium(c, r, u, w, t, d, h);
+      collide(c, d, h);
+    } else {
+#pragma unroll
+      for (int q = 0; q < 9; ++q) d[q] = R(0);
+#pragma unroll
+      for (int q = 0; q < 5; ++q) h[q] = R(0);
+    }
+#pragma unroll
+    for (int q = 0; q < 9; ++q) dst[q * g.plane + i] = from_r<S, R>(d[q]);
+#pragma unroll
+    for (int q = 0; q < 5; ++q) dst[(9 + q) * g.plane + i] = from_r<S, R>(h[q]);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Macroscopic fields from a post-collision state, in FP64:
+//   rho = rho0 + sum d*, T = T0 + sum h* - Q/2, u = (sum d* e - F/2)/rho
+// (the collision adds F to the first moments and Q to the zeroth thermal one).
+// ---------------------------------------------------------------------------
+template <typename S>
+__device__ __forceinline__ void node_macros(const DevCoef& c, const S* __restrict__ b,
+                                            long long plane, long long i, double& rho, double& ux,
+                                            double& uy, double& T) {
+  double f[9], s = 0.0;
+#pragma unroll
+  for (int q = 0; q < 9; ++q) f[q] = (double)to_r(b[q * plane + i]);
+#pragma unroll
+  for (int q = 9; q < 14; ++q) s += (double)to_r(b[q * plane + i]);
+  T = c.T0 + s - 0.5 * c.Q;
+  const double Fx = c.Fvx, Fy = c.Fvy + c.rho0 * c.gbeta * (T - c.T0);
+  const double dr = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
+  rho = c.rho0 + dr;
+  const double jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
+  const double jy = (f[2] - f[4]) + (f[5] - f[7]) + (f[6] - f[8]);
+  ux = (jx - 0.5 * Fx) / rho;
+  uy = (jy - 0.5 * Fy) / rho;
+}
+
+template <typename S>
+__global__ void moments_kernel(const DevGeom g, const DevCoef c, const S* __restrict__ b,
+                               double* __restrict__ rho, double* __restrict__ ux,
+                               double* __restrict__ uy, double* __restrict__ T) {
+  const long long n = (long long)g.ny * g.nx;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+       k += (long long)gridDim.x * blockDim.x) {
+    const int y = (int)(k / g.nx), x = (int)(k - (long long)y * g.nx);
+    const long long i = (long long)y * g.pitch + x;
+    double r = 0, u = 0, v = 0, t = 0;
+    if (!g.flags || !(g.flags[i] & kFlagSolid)) node_macros(c, b, g.plane, i, r, u, v, t);
+    if (rho) rho[k] = r;
+    if (ux) ux[k] = u;
+    if (uy) uy[k] = v;
+    if (T) T[k] = t;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Deterministic FP64 reductions: each block writes its partial sums; a single
+// block adds the partials in index order.
+// ---------------------------------------------------------------------------
+constexpr int kRedThreads = 256;
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <int W>
+__device__ __forceinline__ void block_sum_store(double (&acc)[W], double* out) {
+  __shared__ double sh[kRedThreads / 32][W];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < W; ++k) {
+    const double s = warp_sum(acc[k]);
+    if (lane == 0) sh[wid][k] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x < W) {
+    double s = 0.0;
+    for (int w = 0; w < kRedThreads / 32; ++w) s += sh[w][threadIdx.x];
+    out[threadIdx.x] = s;
+  }
+}
+
+template <typename S>
+__global__ void __launch_bounds__(kRedThreads)
+    residual_kernel(const DevGeom g, const DevCoef c, const S* __restrict__ cur,
+                    const S* __restrict__ prev, double* __restrict__ partials) {
+  double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  const long long n = (long long)g.ny * g.nx;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+       k += (long long)gridDim.x * blockDim.x) {
+    const int y = (int)(k / g.nx), x = (int)(k - (long long)y * g.nx);
+    const long long i = (long long)y * g.pitch + x;
+    if (g.flags && (g.flags[i] & kFlagSolid)) continue;
+    double r1, u1, v1, t1, r0, u0, v0, t0;
+    node_macros(c, cur, g.plane, i, r1, u1, v1, t1);
+    node_macros(c, prev, g.plane, i, r0, u0, v0, t0);
+    acc[0] += (t1 - t0) * (t1 - t0);
+    acc[1] += t1 * t1;
+    acc[2] += (u1 - u0) * (u1 - u0);
+    acc[3] += u1 * u1;
+    acc[4] += (v1 - v0) * (v1 - v0);
+    acc[5] += v1 * v1;
+    if (!isfinite(r1) || !isfinite(u1) || !isfinite(v1) || !isfinite(t1)) acc[6] += 1.0;
+  }
+  block_sum_store<8>(acc, partials + 8 * blockIdx.x);
+}
+
+template <typename S>
+__global__ void __launch_bounds__(kRedThreads)
+    nusselt_kernel(const DevGeom g, const DevCoef c, const S* __restrict__ b,
+                   const NuLink* __restrict__ links, int nlinks, double* __restrict__ partials) {
+  double acc[2] = {0, 0};
+  const Co<double> cd = make_co<double>(c);
+  for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < nlinks; l += gridDim.x * blockDim.x) {
+    const NuLink L = links[l];
+    const double T1 = node_T(b, g.plane, L.own, cd);
+    const bool have2 = L.second >= 0;
+    const double T2 = have2 ? node_T(b, g.plane, L.second, cd) : 0.0;
+    const double Tw = wall_temperature(L.b1, L.b2, L.b3, L.ne, T1, T2, have2);
+    const double grad = have2 ? (8.0 * Tw - 9.0 * T1 + T2) / (3.0 * L.ne)  // Eq. 27
+                              : (Tw - T1) / (0.5 * L.ne);
+    acc[0] += grad;
+    acc[1] += isfinite(grad) ? 0.0 : 1.0;
+  }
+  block_sum_store<2>(acc, partials + 2 * blockIdx.x);
+}
+
+// ---------------------------------------------------------------------------
+// Launchers for one storage type
+// ---------------------------------------------------------------------------
+template <typename S>
+struct LaunchImpl {
+  static constexpr int V = Traits<S>::V;
+
+  static cudaError_t step(const StepArgs& a, cudaStream_t s) {
+    const int nodes_per_block = kStepThreads * V;
+    dim3 grid((a.g.nx + nodes_per_block - 1) / nodes_per_block, a.g.ny);
+    if (a.g.flags)
+      step_kernel<S, true><<<grid, kStepThreads, 0, s>>>(a);
+    else
+      step_kernel<S, false><<<grid, kStepThreads, 0, s>>>(a);
+    return cudaGetLastError();
+  }
+
+  static int blocks_for(long long n, int threads) {
+    long long b = (n + threads - 1) / threads;
+    if (b > 4096) b = 4096;
+    if (b < 1) b = 1;
+    return (int)b;
+  }
+
+  static cudaError_t init(const DevGeom& g, const DevCoef& c, void* dst, const double* rho,
+                          const double* ux, const double* uy, const double* T, cudaStream_t s) {
+    const long long n = (long long)g.ny * g.pitch;
+    init_kernel<S><<<blocks_for(n, 256), 256, 0, s>>>(g, c, static_cast<S*>(dst), rho, ux, uy, T);
+    return cudaGetLastError();
+  }
+
+  static cudaError_t moments(const DevGeom& g, const DevCoef& c, const void* buf, double* rho,
+                             double* ux, double* uy, double* T, cudaStream_t s) {
+    const long long n = (long long)g.ny * g.nx;
+    moments_kernel<S><<<blocks_for(n, 256), 256, 0, s>>>(g, c, static_cast<const S*>(buf), rho,
+                                                          ux, uy, T);
+    return cudaGetLastError();
+  }
+
+  static cudaError_t residual(const DevGeom& g, const DevCoef& c, const void* cur,
+                              const void* prev, double* partials, int nblocks, cudaStream_t s) {
+    residual_kernel<S><<<nblocks, kRedThreads, 0, s>>>(g, c, static_cast<const S*>(cur),
+                                                        static_cast<const S*>(prev), partials);
+    return cudaGetLastError();
+  }
+
+  static cudaError_t nusselt(const DevGeom& g, const DevCoef& c, const void* buf,
+                             const NuLink* links, int nlinks, double* partials, int nblocks,
+                             cudaStream_t s) {
+    nusselt_kernel<S><<<nblocks, kRedThreads, 0, s>>>(g, c, static_cast<const S*>(buf), links,
+                                                       nlinks, partials);
+    return cudaGetLastError();
+  }
+
+  static Launchers table() {
+    Launchers L;
+    L.vec = V;
+    L.step = &step;
+    L.init = &init;
+    L.moments = &moments;
+    L.residual = &residual;
+    L.nusselt = &nusselt;
+    L.elem_bytes = sizeof(S);
+    return L;
+  }
+};
+
+}  // namespace clbm

@@ -1,0 +1,30 @@
+// FP64 storage and FP64 collision, plus the fixed-order partial-sum reduction.
+#include "clbm_kernels.cuh"
+
+namespace clbm {
+
+const Launchers kLaunchF64 = LaunchImpl<double>::table();
+
+// One block adds nblocks rows of `width` partials in index order, so a
+// reduction gives the same bits on every run.
+__global__ void __launch_bounds__(kRedThreads)
+    reduce_partials_kernel(const double* __restrict__ partials, int nblocks, int width,
+                           double* __restrict__ out) {
+  for (int k = 0; k < width; ++k) {
+    double acc[1] = {0.0};
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) acc[0] += partials[(long long)b * width + k];
+    __shared__ double tmp[1];
+    block_sum_store<1>(acc, tmp);
+    __syncthreads();
+    if (threadIdx.x == 0) out[k] = tmp[0];
+    __syncthreads();
+  }
+}
+
+cudaError_t launch_reduce_partials(const double* partials, int nblocks, int width, double* out,
+                                   cudaStream_t s) {
+  reduce_partials_kernel<<<1, kRedThreads, 0, s>>>(partials, nblocks, width, out);
+  return cudaGetLastError();
+}
+
+}  // namespace clbm

@@ -103,6 +103,7 @@ class Workload:
     init: Fields
     length: float = 1.0  # characteristic length H for Nusselt numbers
     dT: float = 1.0      # characteristic temperature difference
+    u_scale: float = 0.1  # characteristic velocity (U of Sec. 3.3 for buoyant flows)
 
 
 def dirichlet(T: float) -> Tuple[float, float, float]:
@@ -346,7 +347,8 @@ def poiseuille_channel(ny: int = 8, nu: float = 0.1, Fx: float = 1e-5, nx: int =
     p = Params(nx=nx, ny=ny, periodic_x=1, s_nu=s_nu, s_b=s_nu if s_b is None else s_b,
                lambda1=lambda1, Fvx=Fx, T0=Tw)
     g = Geometry(tbc=[dirichlet(Tw)], side_tbc=(-1, -1, 0, 0))
-    return Workload(f"poiseuille_{ny}", p, g, Fields(T=np.full((ny, nx), Tw)), length=float(ny))
+    return Workload(f"poiseuille_{ny}", p, g, Fields(T=np.full((ny, nx), Tw)), length=float(ny),
+                    u_scale=Fx * ny * ny / (8.0 * nu))
 
 
 def poiseuille_exact(ny: int, nu: float, Fx: float, rho0: float = 1.0) -> np.ndarray:
@@ -367,7 +369,8 @@ def periodic_box(nx: int = 16, ny: int = 12, seed: int = 7, amp: float = 0.02,
     p = Params(nx=nx, ny=ny, periodic_x=1, periodic_y=1, s_nu=s_nu, lambda1=lambda1,
                T0=0.5, gbeta=gbeta, Q=Q, Fvx=Fvx)
     g = Geometry(tbc=[dirichlet(0.0)], side_tbc=(-1, -1, -1, -1))
-    return Workload(f"periodic_{nx}x{ny}", p, g, Fields(rho=rho, ux=ux, uy=uy, T=T))
+    return Workload(f"periodic_{nx}x{ny}", p, g, Fields(rho=rho, ux=ux, uy=uy, T=T), dT=0.5,
+                    u_scale=amp)
 
 
 def random_fields(nx: int, ny: int, seed: int, amp: float = 0.02, T_mid: float = 0.5,
@@ -387,7 +390,8 @@ def obstacle_channel(nx: int = 37, ny: int = 19, seed: int = 3) -> Workload:
     g = Geometry(tbc=tbc, side_tbc=(0, 1, 3, 2), solid=solid, link_node=ln, link_dir=ld,
                  link_ne=le, link_tbc=lt)
     p = Params(nx=nx, ny=ny, s_nu=1.2, lambda1=1.3, T0=0.5, gbeta=2e-4, Q=3e-5, Fvx=1e-5)
-    return Workload(f"obstacle_{nx}x{ny}", p, g, random_fields(nx, ny, seed, amp=0.01))
+    return Workload(f"obstacle_{nx}x{ny}", p, g, random_fields(nx, ny, seed, amp=0.01), dT=1.0,
+                    u_scale=0.01)
 
 
 def link_arrays(geom: Geometry) -> Tuple[np.ndarray, np.ndarray, np.ndarray, np.ndarray]:

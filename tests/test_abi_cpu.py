@@ -1,0 +1,55 @@
+"""CPU checks of the C ABI library: it builds for sm_103a, loads, exports every
+entry point declared in include/clbm.h, and rejects invalid descriptions
+before touching the GPU (no compute call is made here)."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+from paper_1801_04577_gb300 import build, clbm
+from paper_1801_04577_gb300 import inputs as I
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "clbm.h")).read()
+    return sorted(set(re.findall(r"^\s*(?:const\s+char\s*\*|clbm_status)\s+(clbm_\w+)\s*\(", src, re.M)))
+
+
+def test_library_builds_and_exports_all_declared_symbols():
+    path = build.build()
+    assert os.path.exists(path)
+    lib = C.CDLL(path)
+    names = declared_functions()
+    assert len(names) >= 10
+    for name in names:
+        assert hasattr(lib, name), name
+    assert set(names) == set(clbm.EXPORTS)
+
+
+def test_status_strings():
+    L = clbm.load()
+    assert L.clbm_status_string(0) == b"CLBM_OK"
+    assert L.clbm_status_string(4) == b"CLBM_EUNSTABLE"
+
+
+@pytest.mark.parametrize("field,value", [("nx", 0), ("ny", -3), ("s_nu", 2.5), ("lambda1", 0.0),
+                                         ("rho0", -1.0), ("cT2", 0.7), ("precision", 9)])
+def test_create_rejects_invalid_params(field, value):
+    p = clbm.make_params(I.natural_convection_cavity(16).params, "f32")
+    setattr(p, field, value)
+    L = clbm.load()
+    ctx = C.c_void_p()
+    st = L.clbm_create(C.byref(p), None, C.byref(ctx))
+    assert st == clbm.CLBM_EINVAL
+    assert not ctx.value
+
+
+def test_null_arguments():
+    L = clbm.load()
+    assert L.clbm_create(None, None, None) == clbm.CLBM_EINVAL
+    assert L.clbm_destroy(None) == clbm.CLBM_OK
+    assert L.clbm_step(None, 1) == clbm.CLBM_EINVAL
+    assert L.clbm_last_error(None) == b""

@@ -1,0 +1,163 @@
+"""Parity of the CUDA library (through the C ABI) with the FP64 oracle.
+
+Tolerances: FP64 storage/collision within 1e-12 of the oracle and FP32 within
+1e-5, per field, as max-norm relative to the field's largest value (the
+density as rho - rho0 relative to rho0).  Cases cover several warp tiles, ragged
+row lengths, both kinds of walls, periodic seams, masks with listed links,
+curved walls, the heat source and the body force.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1801_04577_gb300 import clbm
+from paper_1801_04577_gb300 import inputs as I
+
+from _parity import TOL, compare, rel_inf, run_pair
+
+pytestmark = pytest.mark.gpu
+
+
+def _assert_within(errs, tol, label):
+    bad = {k: v for k, v in errs.items() if not (v <= tol)}
+    assert not bad, f"{label}: errors {errs} exceed {tol}"
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+def test_cavity_64_ra1e4_10000_steps(precision):
+    """Differentially heated cavity, 64^2, Ra = 1e4, 10,000 steps (Sec. 3.3 setup)."""
+    w = I.natural_convection_cavity(64, 1e4)
+    errs, (s, o) = run_pair(w, 10000, precision)
+    _assert_within(errs, TOL[precision], f"cavity {precision}")
+    tol_nu = 1e-11 if precision == "f64" else 1e-4
+    for side in (0, 1, 2, 3):
+        a = s.nusselt(side, 64, 1.0)
+        b = o.nusselt(side, 64, 1.0)
+        assert abs(a - b) <= tol_nu * max(1.0, abs(b)), (side, a, b)
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+def test_ragged_mask_links_mixed_walls(precision):
+    """37 x 19 box: walls on all sides with Dirichlet/Robin/Neumann conditions,
+    a solid obstacle with listed links, a source and a body force."""
+    w = I.obstacle_channel()
+    errs, _ = run_pair(w, 400, precision)
+    _assert_within(errs, TOL[precision], f"obstacle {precision}")
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+def test_periodic_x_several_tiles(precision):
+    """Rayleigh-Benard setup on 300 x 70 (ragged against the 128/64-node warp
+    tiles, periodic seam inside a tile), with noise and a source."""
+    w = I.rayleigh_benard(300, 70, Ra=1e5, Q=1e-4, noise=1e-2)
+    errs, _ = run_pair(w, 300, precision)
+    _assert_within(errs, TOL[precision], f"rb {precision}")
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+def test_doubly_periodic_box(precision):
+    w = I.periodic_box(133, 37)
+    errs, _ = run_pair(w, 200, precision)
+    _assert_within(errs, TOL[precision], f"periodic {precision}")
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+def test_annulus_curved_walls(precision):
+    """Annulus with curved Dirichlet (inner) and Robin (outer) walls."""
+    w = I.annulus(96, 2.6, Ra=1e4)
+    errs, _ = run_pair(w, 300, precision)
+    _assert_within(errs, TOL[precision], f"annulus {precision}")
+
+
+def test_annulus_nusselt_and_residual_f64():
+    w = I.annulus(64, 2.6, Ra=1e4)
+    s = clbm.from_workload(w, "f64")
+    o = oracle.from_workload(w)
+    s.step(500)
+    o.step(500)
+    for which in (4, 5):
+        a, b = s.nusselt(which, w.length, 1.0), o.nusselt(which, w.length, 1.0)
+        assert a == pytest.approx(b, rel=1e-11, abs=1e-13)
+    assert s.residual() == pytest.approx(o.residual(), rel=1e-8)
+
+
+@pytest.mark.parametrize("nx", [1, 4, 130])
+def test_diffusion_with_source_exact_gpu(nx, paper_values):
+    """Sec. 3.1 on the GPU, including a single-column lattice (nx = 1)."""
+    pv = paper_values["diffusion_with_source"]
+    for case in pv["cases"]:
+        w = I.diffusion_channel(case["alpha"], L=pv["L"], nx=nx)
+        s = clbm.from_workload(w, "f64")
+        s.step(6000)
+        T = s.moments()[3]
+        Ta = I.diffusion_exact(pv["L"])
+        E2 = np.sqrt(((T - Ta[:, None]) ** 2).sum(axis=0) / (Ta ** 2).sum())
+        assert E2.max() < 1e-12
+
+
+def test_poiseuille_exact_gpu():
+    ny, nu, Fx = 8, 0.1, 1e-5
+    w = I.poiseuille_channel(ny, nu, Fx, nx=64)
+    s = clbm.from_workload(w, "f64")
+    s.step(8000)
+    ux = s.moments()[1]
+    ua = I.poiseuille_exact(ny, nu, Fx)
+    assert np.abs(ux - ua[:, None]).max() / ua.max() < 1e-10
+
+
+def test_residual_and_nusselt_match_oracle_cavity():
+    w = I.natural_convection_cavity(48, 1e4)
+    s = clbm.from_workload(w, "f64")
+    o = oracle.from_workload(w)
+    s.step(700)
+    o.step(700)
+    assert s.residual() == pytest.approx(o.residual(), rel=1e-9)
+    assert s.time == 700
+
+
+def test_zero_steps_is_identity():
+    w = I.obstacle_channel()
+    s = clbm.from_workload(w, "f64")
+    before = s.moments()
+    s.step(0)
+    after = s.moments()
+    for a, b in zip(before, after):
+        np.testing.assert_array_equal(a, b)
+
+
+def test_nan_is_reported_unstable():
+    """A NaN placed in the initial temperature (host input) is caught by the
+    residual check as CLBM_EUNSTABLE."""
+    w = I.obstacle_channel()
+    T = np.full((w.params.ny, w.params.nx), 0.5)
+    T[5, 7] = np.nan
+    w.init = I.Fields(T=T)
+    s = clbm.from_workload(w, "f32")
+    s.step(2)
+    with pytest.raises(clbm.ClbmError) as ei:
+        s.residual()
+    assert ei.value.status == clbm.CLBM_EUNSTABLE
+
+
+def test_invalid_arguments_gpu():
+    w = I.natural_convection_cavity(16, 1e4)
+    s = clbm.Solver(w.params, None, "f32")
+    with pytest.raises(clbm.ClbmError) as ei:
+        s.step(1)  # walls not described yet
+    assert ei.value.status == clbm.CLBM_EINVAL
+    with pytest.raises(clbm.ClbmError):
+        clbm.clbm_set_boundaries(s.ctx, None, w.geom.tbc, (0, 1, 2, 7))
+    with pytest.raises(clbm.ClbmError):
+        s.residual()  # no step since initialisation
+
+
+def test_full_size_rayleigh_benard_f32_against_oracle():
+    """The benchmark lattice itself (4096 x 2048, FP32, bench launch
+    configuration): three steps compared node by node with the FP64 oracle."""
+    w = I.rayleigh_benard(4096, 2048)
+    s = clbm.from_workload(w, "f32")
+    o = oracle.from_workload(w)
+    s.step(3)
+    o.step(3)
+    errs = compare(w, s.moments(), o.moments())
+    _assert_within(errs, TOL["f32"], "rb4096 f32")
