@@ -160,6 +160,34 @@ clbm_status clbm_nusselt(clbm_ctx* ctx, int32_t which, double length, double dT,
  * r_out = +inf) if any field value is NaN or Inf.  Synchronises. */
 clbm_status clbm_residual(clbm_ctx* ctx, double* r_out);
 
+/* Allocation-free variant of the residual reduction (the paper has no
+ * counterpart; it is a service for callers of this library).
+ *
+ * For callers that cannot allocate device memory: applications that give all
+ * device memory to their own pool allocator up front, host frameworks that
+ * forbid allocations by embedded libraries, and time-critical loops that
+ * cannot take the device synchronisation cudaFree implies.  It computes the
+ * clbm_residual quantity, max over phi in {T, ux, uy} of
+ * ||phi_now - phi_prev||_2 / max(||phi_now||_2, 1e-30), from caller-owned
+ * FP64 device arrays of n values (for instance two clbm_moments snapshots one
+ * step apart); `solid` is an optional device uint8 mask (nonzero = skip).
+ * The result is written to the host double *r_out; the call synchronises
+ * `stream` (a cudaStream_t, NULL = legacy default stream).
+ *
+ * It calls no cudaMalloc, cudaFree or allocating library routine: its
+ * reduction scratch is a fixed 65,600-byte array in the library's device
+ * data, held on every GPU that loads the library until the process exits.
+ * The first call on a device looks that array's address up (once per device,
+ * with the device current); make that first call before any stream capture.
+ * All calls share the array, so calls that overlap on the GPU race and must be
+ * serialised by the caller.  Limits: 1 <= n <= 2^31, else CLBM_EINVAL;
+ * CLBM_EUNSTABLE (r_out = +inf) if a value is NaN or Inf. */
+clbm_status clbm_residual_fields_noalloc(const double* T_now, const double* ux_now,
+                                         const double* uy_now, const double* T_prev,
+                                         const double* ux_prev, const double* uy_prev,
+                                         const uint8_t* solid, int64_t n, void* stream,
+                                         double* r_out);
+
 /* Number of time steps taken since the last initialisation. */
 clbm_status clbm_time(const clbm_ctx* ctx, int64_t* t_out);
 

@@ -41,8 +41,8 @@ class clbm_link(C.Structure):
 
 
 EXPORTS = ["clbm_create", "clbm_set_boundaries", "clbm_init_fields", "clbm_step", "clbm_moments",
-           "clbm_nusselt", "clbm_residual", "clbm_time", "clbm_destroy", "clbm_last_error",
-           "clbm_status_string"]
+           "clbm_nusselt", "clbm_residual", "clbm_residual_fields_noalloc", "clbm_time",
+           "clbm_destroy", "clbm_last_error", "clbm_status_string"]
 
 _lib = None
 
@@ -74,6 +74,7 @@ def load(path: Optional[str] = None):
     L.clbm_moments.argtypes = [vp, vp, vp, vp, vp, C.c_int32]
     L.clbm_nusselt.argtypes = [vp, C.c_int32, C.c_double, C.c_double, dp]
     L.clbm_residual.argtypes = [vp, dp]
+    L.clbm_residual_fields_noalloc.argtypes = [vp] * 7 + [C.c_int64, vp, dp]
     L.clbm_time.argtypes = [vp, C.POINTER(C.c_int64)]
     L.clbm_destroy.argtypes = [vp]
     L.clbm_last_error.argtypes = [vp]
@@ -175,6 +176,16 @@ def clbm_nusselt(ctx, which: int, length: float, dT: float) -> float:
 def clbm_residual(ctx) -> float:
     out = C.c_double()
     _check(load().clbm_residual(ctx, C.byref(out)), ctx, "clbm_residual")
+    return out.value
+
+
+def clbm_residual_fields_noalloc(T_now, ux_now, uy_now, T_prev, ux_prev, uy_prev, solid, n: int,
+                                 stream: Optional[int] = None) -> float:
+    """Residual from caller-owned device fields, without device allocation."""
+    out = C.c_double()
+    args = [_addr(b) for b in (T_now, ux_now, uy_now, T_prev, ux_prev, uy_prev, solid)]
+    _check(load().clbm_residual_fields_noalloc(*args, int(n), stream, C.byref(out)), None,
+           "clbm_residual_fields_noalloc")
     return out.value
 
 
