@@ -239,7 +239,7 @@ def run_native(args):
     # would replace by a private stream)
     stream = torch.cuda.Stream(dev)
     torch.cuda.set_stream(stream)
-    s = clbm.from_workload(w, args.precision, stream=stream.cuda_stream)
+    s = clbm.from_workload(w, args.precision, stream=stream.cuda_stream, rounding=args.rounding)
     s.step(args.warmup)
     torch.cuda.synchronize()
     barrier()
@@ -332,6 +332,8 @@ def main():
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--precision", choices=list(ELEM_BYTES), default="f32")
     ap.add_argument("--workload", default="rb4096")
+    ap.add_argument("--rounding", type=int, choices=[0, 1], default=0,
+                    help="16-bit storage: 0 = nearest even, 1 = stochastic")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()

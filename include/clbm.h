@@ -53,12 +53,15 @@ typedef enum {
 /* Storage precision of the distributions.  Every format stores deviations
  * from the rest state (f_i - w_i rho0, g_i - w^T_i T0, with w the D2Q9
  * weights 4/9, 1/9, 1/36 and w^T = (1 - 2 cT2, cT2/2 x4)).  The collision is
- * computed in FP64 for CLBM_F64 and in FP32 for every other format. */
+ * computed in FP64 for CLBM_F64 and in FP32 for every other format.  The
+ * 16-bit formats round either to nearest even or stochastically (params
+ * `rounding`); stochastic rounding draws its bits from a counter-based hash of
+ * (step, node, plane), so runs stay reproducible. */
 typedef enum {
   CLBM_F64 = 0,
   CLBM_F32 = 1,
-  CLBM_F16DEV = 2,   /* IEEE binary16 deviations, round to nearest even  */
-  CLBM_BF16DEV = 3   /* bfloat16 deviations, round to nearest even       */
+  CLBM_F16DEV = 2,   /* IEEE binary16 deviations                          */
+  CLBM_BF16DEV = 3   /* bfloat16 deviations                               */
 } clbm_precision;
 
 /* Problem parameters (lattice units).
@@ -78,7 +81,7 @@ typedef struct {
   int32_t nx, ny;
   int32_t periodic_x, periodic_y;
   int32_t precision; /* clbm_precision */
-  int32_t reserved0;
+  int32_t rounding;  /* 16-bit formats: 0 = round to nearest even, 1 = stochastic rounding */
   double s_nu, s_b, s_3, s_4;
   double lambda0, lambda1, lambda2;
   double rho0, T0, gbeta, Fvx, Fvy, Q, cT2;

@@ -24,7 +24,7 @@ PRECISIONS = {"f64": CLBM_F64, "f32": CLBM_F32, "f16": CLBM_F16DEV, "bf16": CLBM
 
 class clbm_params(C.Structure):
     _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("periodic_x", C.c_int32),
-                ("periodic_y", C.c_int32), ("precision", C.c_int32), ("reserved0", C.c_int32),
+                ("periodic_y", C.c_int32), ("precision", C.c_int32), ("rounding", C.c_int32),
                 ("s_nu", C.c_double), ("s_b", C.c_double), ("s_3", C.c_double), ("s_4", C.c_double),
                 ("lambda0", C.c_double), ("lambda1", C.c_double), ("lambda2", C.c_double),
                 ("rho0", C.c_double), ("T0", C.c_double), ("gbeta", C.c_double),
@@ -114,9 +114,10 @@ def _addr(a) -> Optional[int]:
     raise TypeError(f"unsupported buffer type {type(a)}")
 
 
-def make_params(p, precision="f32") -> clbm_params:
+def make_params(p, precision="f32", rounding: int = 0) -> clbm_params:
+    """rounding: 0 = nearest even, 1 = stochastic (16-bit storage only)."""
     prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
-    return clbm_params(p.nx, p.ny, p.periodic_x, p.periodic_y, prec, 0, p.s_nu, p.s_b, p.s_3,
+    return clbm_params(p.nx, p.ny, p.periodic_x, p.periodic_y, prec, int(rounding), p.s_nu, p.s_b, p.s_3,
                        p.s_4, p.lambda0, p.lambda1, p.lambda2, p.rho0, p.T0, p.gbeta, p.Fvx,
                        p.Fvy, p.Q, p.cT2)
 
@@ -210,11 +211,12 @@ def clbm_last_error(ctx) -> str:
 class Solver:
     """One lattice on the GPU, described by ``inputs.Params`` / ``inputs.Geometry``."""
 
-    def __init__(self, params, geom=None, precision="f32", stream: Optional[int] = None, init=None):
+    def __init__(self, params, geom=None, precision="f32", stream: Optional[int] = None, init=None,
+                 rounding: int = 0):
         self.params = params
         self.nx, self.ny = params.nx, params.ny
         self.precision = precision
-        self.ctx = clbm_create(make_params(params, precision), stream)
+        self.ctx = clbm_create(make_params(params, precision, rounding), stream)
         if geom is not None:
             clbm_set_boundaries(self.ctx, geom.solid, geom.tbc, geom.side_tbc, geom.link_node,
                                 geom.link_dir, geom.link_ne, geom.link_tbc)
@@ -262,5 +264,5 @@ class Solver:
         return clbm_time(self.ctx)
 
 
-def from_workload(w, precision="f32", stream=None) -> Solver:
-    return Solver(w.params, w.geom, precision, stream, w.init)
+def from_workload(w, precision="f32", stream=None, rounding: int = 0) -> Solver:
+    return Solver(w.params, w.geom, precision, stream, w.init, rounding)

@@ -179,6 +179,7 @@ clbm_status clbm_create(const clbm_params* params, void* stream, clbm_ctx** out)
   if (p.nx < 1 || p.ny < 1 || p.ny > 65535 || (long long)p.nx * p.ny > (1LL << 31))
     return CLBM_EINVAL;
   auto rate_ok = [](double s) { return std::isfinite(s) && s > 0.0 && s < 2.0; };
+  if (p.rounding != 0 && p.rounding != 1) return CLBM_EINVAL;
   if (!rate_ok(p.s_nu) || !rate_ok(p.s_b) || !rate_ok(p.s_4) || !rate_ok(p.lambda1) ||
       !(std::isfinite(p.lambda0)) || !(p.rho0 > 0) || !(p.cT2 > 0 && p.cT2 < 0.5))
     return CLBM_EINVAL;
@@ -423,9 +424,11 @@ clbm_status clbm_step(clbm_ctx* c, int64_t nsteps) {
   StepArgs a;
   a.g = make_geom(c);
   a.c = make_coef(c);
+  a.stochastic = c->p.rounding;
   for (int64_t s = 0; s < nsteps; ++s) {
     a.src = c->buf[c->cur];
     a.dst = c->buf[c->cur ^ 1];
+    a.seed = (uint32_t)(c->t * 0x9E3779B1ull) ^ (uint32_t)(c->t >> 32);
     cudaError_t e = c->L->step(a, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "step kernel launch");
     c->cur ^= 1;

@@ -41,6 +41,8 @@ struct StepArgs {
   DevCoef c;
   const void* src;  // post-collision state at time t
   void* dst;        // post-collision state at time t + 1
+  uint32_t seed;    // per-step key of the stochastic-rounding hash
+  int stochastic;   // 16-bit stores: 0 = nearest even, 1 = stochastic
 };
 
 // One Nusselt link, prepared on the host: node index (pitch layout) of x_f,

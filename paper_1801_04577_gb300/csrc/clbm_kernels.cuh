@@ -161,6 +161,50 @@ __device__ __forceinline__ void stv(__nv_bfloat16* p, const float (&o)[4]) {
 }
 
 // ---------------------------------------------------------------------------
+// Stochastic rounding of 16-bit stores.  Round-to-nearest storage of a state
+// that changes little from step to step rounds the same way every step, and the
+// bias accumulates; stochastic rounding makes each store unbiased.  The random
+// bits come from a counter-based hash of (step, node, plane): the "lowbias32"
+// integer mixer published by C. Wellons ("Prospecting for Hash Functions", 2018).
+// ---------------------------------------------------------------------------
+__host__ __device__ __forceinline__ uint32_t mix32(uint32_t x) {
+  x ^= x >> 16;
+  x *= 0x7feb352du;
+  x ^= x >> 15;
+  x *= 0x846ca68bu;
+  x ^= x >> 16;
+  return x;
+}
+
+// Hardware stochastic rounding of two floats into a packed 16-bit pair
+// (cvt.rs, Blackwell): `lo` lands in the low half (the first element in
+// memory), `hi` in the high half; rbits supplies the random bits.
+__device__ __forceinline__ uint32_t cvt_rs_f16x2(float lo, float hi, uint32_t rbits) {
+  uint32_t d;
+  asm("cvt.rs.satfinite.f16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(hi), "f"(lo), "r"(rbits));
+  return d;
+}
+__device__ __forceinline__ uint32_t cvt_rs_bf16x2(float lo, float hi, uint32_t rbits) {
+  uint32_t d;
+  asm("cvt.rs.satfinite.bf16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(hi), "f"(lo), "r"(rbits));
+  return d;
+}
+
+__device__ __forceinline__ void stv_sr(double* p, const double (&o)[2], uint32_t, uint32_t) {
+  stv(p, o);
+}
+__device__ __forceinline__ void stv_sr(float* p, const float (&o)[4], uint32_t, uint32_t) {
+  stv(p, o);
+}
+__device__ __forceinline__ void stv_sr(__half* p, const float (&o)[4], uint32_t r0, uint32_t r1) {
+  *reinterpret_cast<uint2*>(p) = make_uint2(cvt_rs_f16x2(o[0], o[1], r0), cvt_rs_f16x2(o[2], o[3], r1));
+}
+__device__ __forceinline__ void stv_sr(__nv_bfloat16* p, const float (&o)[4], uint32_t r0,
+                                       uint32_t r1) {
+  *reinterpret_cast<uint2*>(p) = make_uint2(cvt_rs_bf16x2(o[0], o[1], r0), cvt_rs_bf16x2(o[2], o[3], r1));
+}
+
+// ---------------------------------------------------------------------------
 // Constants in the compute type
 // ---------------------------------------------------------------------------
 template <typename R>
@@ -505,8 +549,19 @@ __global__ void __launch_bounds__(kStepThreads) step_kernel(const StepArgs a) {
     for (int q = 0; q < 5; ++q) v[9 + q][k] = h[q];
   }
 
+  S* out = dst + (long long)y * g.pitch + x0;
+  if (sizeof(S) == 2 && a.stochastic) {
+    const uint32_t key = a.seed ^ mix32((uint32_t)((long long)y * g.pitch + x0));
 #pragma unroll
-  for (int q = 0; q < 14; ++q) stv(dst + q * plane + (long long)y * g.pitch + x0, v[q]);
+    for (int q = 0; q < 14; ++q) {
+      const uint32_t r0 = mix32(key + 0x9E3779B9u * (uint32_t)(q + 1));
+      const uint32_t r1 = mix32(r0 ^ 0x85EBCA6Bu);
+      stv_sr(out + q * plane, v[q], r0, r1);
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < 14; ++q) stv(out + q * plane, v[q]);
+  }
 }
 
 // ---------------------------------------------------------------------------

@@ -1,0 +1,106 @@
+"""Reduced-precision storage against the FP64 oracle (stated tolerances).
+
+16-bit formats store deviations from the rest state and collide in FP32.  The
+tolerances below are the stated accuracy of each format (about three times
+the values measured on a GB300):
+
+* steady natural convection, 64^2 cavity, Ra = 1e4, 10,000 steps: field L2
+  errors of (ux, uy, T) and the relative error of the cold-wall Nusselt number;
+* the 256 x 128 Rayleigh-Benard copy of the benchmark cell, 1,000 steps
+  (before the convective instability amplifies rounding differences): L2 of T
+  and the bottom-wall Nusselt number.
+
+With round-to-nearest storage the rounding error of a slowly varying state is
+biased and accumulates; stochastic rounding (rounding = 1) removes the bias.
+Round-to-nearest BF16 is kept only as a documented (poor) reference point.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1801_04577_gb300 import clbm
+from paper_1801_04577_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+# (precision, rounding): (max L2 of ux, uy, T; max relative Nu error)
+CAVITY_TOL = {
+    ("f32", 0): (1e-5, 1e-5),
+    ("f16", 1): (2e-3, 1e-3),
+    ("bf16", 1): (1.5e-2, 6e-2),
+    ("f16", 0): (3e-2, 1.5e-2),
+    ("bf16", 0): (0.4, 0.8),
+}
+RB_TOL = {  # (L2 of T, relative Nu error at the bottom wall)
+    ("f32", 0): (1e-4, 2e-3),
+    ("f16", 1): (1e-3, 1e-2),
+    ("bf16", 1): (6e-3, 0.1),
+}
+
+
+@pytest.fixture(scope="module")
+def cavity_ref():
+    w = I.natural_convection_cavity(64, 1e4)
+    o = oracle.from_workload(w)
+    o.step(10000)
+    return w, o.moments(), -o.nusselt(1, 64, 1.0)
+
+
+@pytest.fixture(scope="module")
+def rb_ref():
+    w = I.rayleigh_benard(256, 128)
+    o = oracle.from_workload(w)
+    o.step(1000)
+    return w, o.moments(), o.nusselt(2, w.length, 1.0)
+
+
+def _l2(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.mark.parametrize("precision,rounding", list(CAVITY_TOL))
+def test_cavity_reduced_precision(cavity_ref, precision, rounding):
+    w, ref, nu_ref = cavity_ref
+    s = clbm.from_workload(w, precision, rounding=rounding)
+    s.step(10000)
+    got = s.moments()
+    nu = -s.nusselt(1, 64, 1.0)
+    tol_l2, tol_nu = CAVITY_TOL[(precision, rounding)]
+    errs = [_l2(a, b) for a, b in zip(got[1:], ref[1:])]
+    assert all(np.isfinite(errs))
+    assert max(errs) < tol_l2, (precision, rounding, errs)
+    assert abs(nu - nu_ref) / abs(nu_ref) < tol_nu, (precision, rounding, nu, nu_ref)
+
+
+@pytest.mark.parametrize("precision,rounding", list(RB_TOL))
+def test_rayleigh_benard_copy_reduced_precision(rb_ref, precision, rounding):
+    w, ref, nu_ref = rb_ref
+    s = clbm.from_workload(w, precision, rounding=rounding)
+    s.step(1000)
+    got = s.moments()
+    nu = s.nusselt(2, w.length, 1.0)
+    tol_T, tol_nu = RB_TOL[(precision, rounding)]
+    assert _l2(got[3], ref[3]) < tol_T
+    assert abs(nu - nu_ref) / abs(nu_ref) < tol_nu
+
+
+def test_stochastic_rounding_is_reproducible():
+    """The rounding bits come from a hash of (step, node, plane): two runs agree bit for bit."""
+    w = I.obstacle_channel()
+    runs = []
+    for _ in range(2):
+        s = clbm.from_workload(w, "bf16", rounding=1)
+        s.step(300)
+        runs.append(s.moments())
+    for a, b in zip(*runs):
+        np.testing.assert_array_equal(a, b)
+
+
+def test_stochastic_rounding_beats_nearest_on_steady_cavity(cavity_ref):
+    w, ref, _ = cavity_ref
+    err = {}
+    for rounding in (0, 1):
+        s = clbm.from_workload(w, "bf16", rounding=rounding)
+        s.step(10000)
+        err[rounding] = _l2(s.moments()[3], ref[3])
+    assert err[1] < 0.1 * err[0]
