@@ -27,6 +27,8 @@ import sys
 import tempfile
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -324,6 +326,59 @@ def run_native(args):
     return 0
 
 
+def run_batch(args):
+    """Batched solve of the seeded 512-cavity set: --steps is the step cap."""
+    import torch
+
+    from paper_1801_04577_gb300 import clbm
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py: no CUDA device (the library has no CPU path)")
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    ws = I.random_cavities(args.batch_size)
+    nodes = np.array([w.params.nx * w.params.ny for w in ws], dtype=np.int64)
+    t0 = time.perf_counter()
+    b = clbm.Batch(ws, args.precision, rounding=args.rounding, autotune=True, stream=stream.cuda_stream)
+    t_create = time.perf_counter() - t0
+    torch.cuda.synchronize()
+    sampler = ClockSampler(device_index(0))
+    sampler.start()
+    t0 = time.perf_counter()
+    conv, res, steps = b.solve(args.tol, args.steps, check_every=args.check_every)
+    el = time.perf_counter() - t0
+    clocks = sampler.stop()
+    per = np.where(conv > 0, conv, steps)
+    per = np.where(conv == -2, 0, per)
+    updates = float((nodes * per).sum())
+    value = updates / el / 1e6
+    peak, peak_kind = measured_peak()
+    bytes_lu = 28 * ELEM_BYTES[args.precision]
+    widths = [b.tile_width(i) for i in range(len(ws))]
+    line = {"metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": 1,
+            "steps": int(steps), "warmup": 0, "ms_per_step": el / max(steps, 1) * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": DTYPE[args.precision], "data": "synthetic",
+            "config": {"workload": f"batch_{len(ws)}_random_cavities_{args.precision}",
+                       "total_nodes": int(nodes.sum()), "tol": args.tol, "step_cap": args.steps,
+                       "check_every": args.check_every, "rounding": args.rounding},
+            "roofline": {"bound": "hbm", "achieved": bytes_lu * updates / el / 1e9, "peak": peak,
+                         "unit": "GB/s", "frac": bytes_lu * updates / el / 1e9 / peak,
+                         "traffic": None, "kernel": "clbm::batch_step_kernel (whole solve)",
+                         "peak_kind": peak_kind},
+            "batch": {"converged": int((conv > 0).sum()), "diverged": int((conv == -2).sum()),
+                      "not_converged": int((conv == -1).sum()),
+                      "median_steps_converged": float(np.median(conv[conv > 0])) if (conv > 0).any() else None,
+                      "create_s": t_create, "solve_s": el,
+                      "tile_widths": {str(k): widths.count(k) for k in (32, 64, 128)}},
+            "gpu_launches": None}
+    if clocks is not None:
+        line["clocks"] = clocks
+    print(json.dumps(line), flush=True)
+    b.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -336,11 +391,16 @@ def main():
                     help="16-bit storage: 0 = nearest even, 1 = stochastic")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--batch-size", type=int, default=512)
+    ap.add_argument("--tol", type=float, default=1e-6)
+    ap.add_argument("--check-every", type=int, default=100)
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("bench.py: at least 3 warm-up steps are required")
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch512":
+        return run_batch(args)
     return run_native(args)
 
 

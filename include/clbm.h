@@ -191,6 +191,65 @@ clbm_status clbm_residual_fields_noalloc(const double* T_now, const double* ux_n
                                          const uint8_t* solid, int64_t n, void* stream,
                                          double* r_out);
 
+/* ---------------------------------------------------------------------
+ * Batched solves: many independent lattices (sizes, rates, walls may all
+ * differ) advanced together by the same kernel launches.
+ * ------------------------------------------------------------------- */
+typedef struct clbm_batch clbm_batch;
+
+/* One lattice of a batch.  params.precision and params.rounding must be the
+ * same for every item.  solid / tbc / side_tbc / links follow
+ * clbm_set_boundaries; rho, ux, uy, T are host FP64 [ny][nx] initial fields
+ * (NULL = rest value), used as in clbm_init_fields.  All host data is copied
+ * during clbm_batch_create. */
+typedef struct {
+  clbm_params params;
+  const uint8_t* solid;
+  const clbm_tbc* tbc;
+  int32_t n_tbc;
+  int32_t side_tbc[4];
+  int32_t n_links;
+  const clbm_link* links;
+  const double* rho;
+  const double* ux;
+  const double* uy;
+  const double* T;
+} clbm_batch_item;
+
+/* Create a batch of n lattices in one device arena (two ping-pong buffers).
+ * autotune != 0 times the batched step with tile widths of 32, 64 and 128
+ * nodes per warp for each class of row length (<= 48, <= 96, <= 192, > 192
+ * nodes) and keeps the fastest; otherwise every lattice uses 128 (64 for
+ * FP64).  `stream` as in clbm_create.  Errors as clbm_create and
+ * clbm_set_boundaries. */
+clbm_status clbm_batch_create(const clbm_batch_item* items, int32_t n, int32_t autotune,
+                              void* stream, clbm_batch** out);
+
+/* Advance every lattice until its steady-state residual (the clbm_residual
+ * quantity, checked every check_every steps, rounded up to an even number)
+ * falls below tol, or until max_steps steps (the last check may overrun by
+ * less than check_every).  Each check_every block of steps is one replay of a
+ * captured CUDA graph; converged lattices leave the device-side work list.
+ * Outputs (host arrays of n, may be NULL): conv_steps[i] = step count at
+ * which lattice i converged, -1 if it did not, -2 if it diverged (NaN/Inf);
+ * residuals[i] = its last computed residual; *steps_run = steps taken.
+ * The lattices keep their final state (read it through clbm_batch_lattice). */
+clbm_status clbm_batch_solve(clbm_batch* b, double tol, int64_t max_steps, int32_t check_every,
+                             int64_t* conv_steps, double* residuals, int64_t* steps_run);
+
+/* Context view of lattice i (owned by the batch: do not destroy it) for
+ * clbm_moments, clbm_nusselt, clbm_residual, clbm_init_fields or clbm_step. */
+clbm_status clbm_batch_lattice(clbm_batch* b, int32_t i, clbm_ctx** view);
+
+/* Nodes per warp tile chosen for lattice i (32, 64 or 128). */
+clbm_status clbm_batch_tile_width(const clbm_batch* b, int32_t i, int32_t* nodes_per_warp);
+
+/* Free the batch, its views and its arena (NULL is allowed). */
+clbm_status clbm_batch_destroy(clbm_batch* b);
+
+/* Message of the last failure on this batch ("" if none). */
+const char* clbm_batch_last_error(const clbm_batch* b);
+
 /* Number of time steps taken since the last initialisation. */
 clbm_status clbm_time(const clbm_ctx* ctx, int64_t* t_out);
 

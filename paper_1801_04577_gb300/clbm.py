@@ -40,9 +40,18 @@ class clbm_link(C.Structure):
                 ("tbc", C.c_int32), ("reserved", C.c_int32)]
 
 
+class clbm_batch_item(C.Structure):
+    _fields_ = [("params", clbm_params), ("solid", C.c_void_p), ("tbc", C.POINTER(clbm_tbc)),
+                ("n_tbc", C.c_int32), ("side_tbc", C.c_int32 * 4), ("n_links", C.c_int32),
+                ("links", C.POINTER(clbm_link)), ("rho", C.c_void_p), ("ux", C.c_void_p),
+                ("uy", C.c_void_p), ("T", C.c_void_p)]
+
+
 EXPORTS = ["clbm_create", "clbm_set_boundaries", "clbm_init_fields", "clbm_step", "clbm_moments",
-           "clbm_nusselt", "clbm_residual", "clbm_residual_fields_noalloc", "clbm_time",
-           "clbm_destroy", "clbm_last_error", "clbm_status_string"]
+           "clbm_nusselt", "clbm_residual", "clbm_residual_fields_noalloc", "clbm_batch_create",
+           "clbm_batch_solve", "clbm_batch_lattice", "clbm_batch_tile_width", "clbm_batch_destroy",
+           "clbm_batch_last_error", "clbm_time", "clbm_destroy", "clbm_last_error",
+           "clbm_status_string"]
 
 _lib = None
 
@@ -81,8 +90,16 @@ def load(path: Optional[str] = None):
     L.clbm_last_error.restype = C.c_char_p
     L.clbm_status_string.argtypes = [C.c_int]
     L.clbm_status_string.restype = C.c_char_p
+    L.clbm_batch_create.argtypes = [C.POINTER(clbm_batch_item), C.c_int32, C.c_int32, vp, C.POINTER(vp)]
+    L.clbm_batch_solve.argtypes = [vp, C.c_double, C.c_int64, C.c_int32, C.POINTER(C.c_int64), dp,
+                                   C.POINTER(C.c_int64)]
+    L.clbm_batch_lattice.argtypes = [vp, C.c_int32, C.POINTER(vp)]
+    L.clbm_batch_tile_width.argtypes = [vp, C.c_int32, C.POINTER(C.c_int32)]
+    L.clbm_batch_destroy.argtypes = [vp]
+    L.clbm_batch_last_error.argtypes = [vp]
+    L.clbm_batch_last_error.restype = C.c_char_p
     for name in EXPORTS:
-        if name not in ("clbm_last_error", "clbm_status_string"):
+        if name not in ("clbm_last_error", "clbm_status_string", "clbm_batch_last_error"):
             getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -266,3 +283,121 @@ class Solver:
 
 def from_workload(w, precision="f32", stream=None, rounding: int = 0) -> Solver:
     return Solver(w.params, w.geom, precision, stream, w.init, rounding)
+
+
+# --------------------------------------------------------------------------
+# Batched solves
+# --------------------------------------------------------------------------
+def _batch_check(st, b, what):
+    if st != CLBM_OK:
+        L = load()
+        msg = L.clbm_status_string(st).decode()
+        if b is not None and b.value:
+            detail = L.clbm_batch_last_error(b).decode()
+            if detail:
+                msg += ": " + detail
+        raise ClbmError(st, f"{what}: {msg}")
+
+
+def clbm_batch_create(items, autotune: bool = True, stream: Optional[int] = None) -> C.c_void_p:
+    arr = (clbm_batch_item * len(items))(*items)
+    b = C.c_void_p()
+    _batch_check(load().clbm_batch_create(arr, len(items), int(autotune), stream, C.byref(b)), None,
+                 "clbm_batch_create")
+    return b
+
+
+def clbm_batch_solve(b, n: int, tol: float, max_steps: int, check_every: int = 100):
+    conv = (C.c_int64 * n)()
+    res = (C.c_double * n)()
+    steps = C.c_int64()
+    _batch_check(load().clbm_batch_solve(b, float(tol), int(max_steps), int(check_every), conv,
+                                         res, C.byref(steps)), b, "clbm_batch_solve")
+    return np.array(conv[:], dtype=np.int64), np.array(res[:]), steps.value
+
+
+def clbm_batch_lattice(b, i: int) -> C.c_void_p:
+    v = C.c_void_p()
+    _batch_check(load().clbm_batch_lattice(b, int(i), C.byref(v)), b, "clbm_batch_lattice")
+    return v
+
+
+def clbm_batch_tile_width(b, i: int) -> int:
+    w = C.c_int32()
+    _batch_check(load().clbm_batch_tile_width(b, int(i), C.byref(w)), b, "clbm_batch_tile_width")
+    return w.value
+
+
+def clbm_batch_destroy(b):
+    if b is not None and b.value:
+        load().clbm_batch_destroy(b)
+
+
+class Batch:
+    """Many independent lattices (``inputs.Workload`` list) solved together."""
+
+    def __init__(self, workloads, precision="f32", rounding: int = 0, autotune: bool = True,
+                 stream: Optional[int] = None):
+        self.workloads = list(workloads)
+        keep = []
+        items = []
+        for w in self.workloads:
+            p, g = w.params, w.geom
+            shape = (p.ny, p.nx)
+            tbc = (clbm_tbc * max(len(g.tbc), 1))(*[clbm_tbc(*map(float, t)) for t in g.tbc])
+            nl = g.n_links
+            links = (clbm_link * max(nl, 1))()
+            for k in range(nl):
+                links[k] = clbm_link(int(g.link_node[k]), int(g.link_dir[k]), float(g.link_ne[k]),
+                                     int(g.link_tbc[k]), 0)
+            solid = None if g.solid is None else np.ascontiguousarray(g.solid, np.uint8)
+            fields = []
+            for a in (w.init.rho, w.init.ux, w.init.uy, w.init.T):
+                fields.append(None if a is None else
+                              np.ascontiguousarray(np.broadcast_to(a, shape), np.float64))
+            keep.append((tbc, links, solid, fields))
+            it = clbm_batch_item()
+            it.params = make_params(p, precision, rounding)
+            it.solid = None if solid is None else solid.ctypes.data
+            it.tbc = tbc
+            it.n_tbc = len(g.tbc)
+            it.side_tbc = (C.c_int32 * 4)(*[int(v) for v in g.side_tbc])
+            it.n_links = nl
+            it.links = links
+            it.rho, it.ux, it.uy, it.T = [None if a is None else a.ctypes.data for a in fields]
+            items.append(it)
+        self.b = clbm_batch_create(items, autotune, stream)
+        del keep
+
+    def __len__(self):
+        return len(self.workloads)
+
+    def solve(self, tol: float, max_steps: int, check_every: int = 100):
+        return clbm_batch_solve(self.b, len(self), tol, max_steps, check_every)
+
+    def view(self, i: int) -> C.c_void_p:
+        return clbm_batch_lattice(self.b, i)
+
+    def moments(self, i: int):
+        w = self.workloads[i]
+        shape = (w.params.ny, w.params.nx)
+        out = [np.empty(shape) for _ in range(4)]
+        clbm_moments(self.view(i), *out)
+        return tuple(out)
+
+    def nusselt(self, i: int, which: int, length: float, dT: float) -> float:
+        return clbm_nusselt(self.view(i), which, length, dT)
+
+    def tile_width(self, i: int) -> int:
+        return clbm_batch_tile_width(self.b, i)
+
+    def close(self):
+        if getattr(self, "b", None) is not None:
+            clbm_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

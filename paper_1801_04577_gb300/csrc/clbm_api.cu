@@ -40,6 +40,7 @@ struct clbm_ctx {
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   void* buf[2] = {nullptr, nullptr};
+  bool borrowed = false;  // buffers owned by a batch arena
   int cur = 0;
   int64_t t = 0;
   bool have_walls = false;
@@ -49,6 +50,8 @@ struct clbm_ctx {
   double* d_lk_ne = nullptr;
   int32_t* d_lk_tbc = nullptr;
   double* d_tbc = nullptr;
+  std::vector<int32_t> h_bnodes;  // nodes the boundary kernel recomputes (pitch layout)
+  int32_t* d_bnodes = nullptr;
   std::vector<uint8_t> h_solid;
   std::vector<clbm_tbc> h_tbc;
   std::vector<clbm_link> h_links;
@@ -130,6 +133,8 @@ static void free_tables(clbm_ctx* c) {
   cudaFree(c->d_lk_ne);
   cudaFree(c->d_lk_tbc);
   cudaFree(c->d_tbc);
+  cudaFree(c->d_bnodes);
+  c->d_bnodes = nullptr;
   c->d_flags = nullptr;
   c->d_slot = nullptr;
   c->d_lk_ne = nullptr;
@@ -137,6 +142,35 @@ static void free_tables(clbm_ctx* c) {
   c->d_tbc = nullptr;
   for (auto& kv : c->nu_lists) cudaFree(kv.second.first);
   c->nu_lists.clear();
+}
+
+// Nodes that the interior kernel cannot update on its own: the first and last
+// column (walls or the periodic seam), the first and last row of a non-periodic
+// y axis, and (masked lattices) every fluid node with a wall or solid among
+// its pull sources.  Solid nodes are never listed.
+static cudaError_t upload_boundary_list(clbm_ctx* c, const std::vector<uint16_t>& flags) {
+  const int nx = c->p.nx, ny = c->p.ny;
+  const bool py = c->p.periodic_y;
+  std::vector<int32_t>& v = c->h_bnodes;
+  v.clear();
+  for (int y = 0; y < ny; ++y) {
+    const bool yedge = !py && (y == 0 || y == ny - 1);
+    for (int x = 0; x < nx; ++x) {
+      const size_t ip = (size_t)y * c->pitch + x;
+      bool need = yedge || x == 0 || x == nx - 1;
+      if (!flags.empty()) {
+        if (flags[ip] & kFlagSolid) continue;
+        need = need || (flags[ip] & 0xFFu);
+      }
+      if (need) v.push_back((int32_t)ip);
+    }
+  }
+  cudaFree(c->d_bnodes);
+  c->d_bnodes = nullptr;
+  if (v.empty()) return cudaSuccess;
+  cudaError_t e = cudaMalloc(&c->d_bnodes, v.size() * sizeof(int32_t));
+  if (e != cudaSuccess) return e;
+  return cudaMemcpy(c->d_bnodes, v.data(), v.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
 }
 
 extern "C" {
@@ -160,8 +194,10 @@ clbm_status clbm_destroy(clbm_ctx* c) {
   if (!c) return CLBM_OK;
   if (c->stream) cudaStreamSynchronize(c->stream);
   free_tables(c);
-  cudaFree(c->buf[0]);
-  cudaFree(c->buf[1]);
+  if (!c->borrowed) {
+    cudaFree(c->buf[0]);
+    cudaFree(c->buf[1]);
+  }
   cudaFree(c->d_fields);
   cudaFree(c->d_part);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
@@ -169,7 +205,8 @@ clbm_status clbm_destroy(clbm_ctx* c) {
   return CLBM_OK;
 }
 
-clbm_status clbm_create(const clbm_params* params, void* stream, clbm_ctx** out) {
+static clbm_status create_impl(const clbm_params* params, void* stream, void* buf_a, void* buf_b,
+                               clbm_ctx** out) {
   if (!out) return CLBM_EINVAL;
   *out = nullptr;
   if (!params) return CLBM_EINVAL;
@@ -193,8 +230,7 @@ clbm_status clbm_create(const clbm_params* params, void* stream, clbm_ctx** out)
     return CLBM_EINVAL;
   }
   c->L = L;
-  const int gran = 32 * L->vec;
-  c->pitch = (p.nx + gran - 1) / gran * gran;
+  c->pitch = view_pitch(p.nx, p.precision);
   c->plane = (long long)p.ny * c->pitch;
   c->buf_bytes = (size_t)14 * (size_t)c->plane * L->elem_bytes;
   c->have_walls = p.periodic_x && p.periodic_y;
@@ -211,12 +247,19 @@ clbm_status clbm_create(const clbm_params* params, void* stream, clbm_ctx** out)
     }
     c->own_stream = true;
   }
+  if (buf_a && buf_b) {
+    c->buf[0] = buf_a;
+    c->buf[1] = buf_b;
+    c->borrowed = true;
+  }
   for (int b = 0; b < 2; ++b) {
-    e = cudaMalloc(&c->buf[b], c->buf_bytes);
-    if (e != cudaSuccess) {
-      cudaGetLastError();
-      clbm_destroy(c);
-      return e == cudaErrorMemoryAllocation ? CLBM_ENOMEM : CLBM_ECUDA;
+    if (!c->borrowed) {
+      e = cudaMalloc(&c->buf[b], c->buf_bytes);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        clbm_destroy(c);
+        return e == cudaErrorMemoryAllocation ? CLBM_ENOMEM : CLBM_ECUDA;
+      }
     }
     e = cudaMemsetAsync(c->buf[b], 0, c->buf_bytes, c->stream);
     if (e != cudaSuccess) {
@@ -230,6 +273,11 @@ clbm_status clbm_create(const clbm_params* params, void* stream, clbm_ctx** out)
     clbm_destroy(c);
     return CLBM_ENOMEM;
   }
+  if (c->plane > (1LL << 31) - 1 || upload_boundary_list(c, {}) != cudaSuccess) {
+    cudaGetLastError();
+    clbm_destroy(c);
+    return CLBM_ENOMEM;
+  }
   clbm_status st = clbm_init_fields(c, nullptr, nullptr, nullptr, nullptr, 0);
   if (st != CLBM_OK) {
     clbm_destroy(c);
@@ -237,6 +285,10 @@ clbm_status clbm_create(const clbm_params* params, void* stream, clbm_ctx** out)
   }
   *out = c;
   return CLBM_OK;
+}
+
+clbm_status clbm_create(const clbm_params* params, void* stream, clbm_ctx** out) {
+  return create_impl(params, stream, nullptr, nullptr, out);
 }
 
 clbm_status clbm_set_boundaries(clbm_ctx* c, const uint8_t* solid, const clbm_tbc* tbc,
@@ -363,6 +415,7 @@ clbm_status clbm_set_boundaries(clbm_ctx* c, const uint8_t* solid, const clbm_tb
       CLBM_CUDA(c, cudaMalloc(&c->d_tbc, t3.size() * sizeof(double)));
       CLBM_CUDA(c, cudaMemcpy(c->d_tbc, t3.data(), t3.size() * sizeof(double), cudaMemcpyHostToDevice));
     }
+    CLBM_CUDA(c, upload_boundary_list(c, flags));
     for (int s = 0; s < 4; ++s) {
       c->side_tbc[s] = sides[s];
       for (int k = 0; k < 3; ++k)
@@ -425,6 +478,8 @@ clbm_status clbm_step(clbm_ctx* c, int64_t nsteps) {
   a.g = make_geom(c);
   a.c = make_coef(c);
   a.stochastic = c->p.rounding;
+  a.bnodes = c->d_bnodes;
+  a.nb = (int)c->h_bnodes.size();
   for (int64_t s = 0; s < nsteps; ++s) {
     a.src = c->buf[c->cur];
     a.dst = c->buf[c->cur ^ 1];
@@ -584,3 +639,43 @@ clbm_status clbm_residual(clbm_ctx* c, double* r_out) {
 }
 
 }  // extern "C"
+
+namespace clbm {
+
+int view_pitch(int nx, int precision) {
+  const Launchers* L = launchers_for(precision);
+  const int gran = 32 * (L ? L->vec : 4);
+  return (nx + gran - 1) / gran * gran;
+}
+
+size_t view_buffer_bytes(int nx, int ny, int precision) {
+  const Launchers* L = launchers_for(precision);
+  if (!L) return 0;
+  return (size_t)14 * (size_t)ny * (size_t)view_pitch(nx, precision) * L->elem_bytes;
+}
+
+clbm_status create_view(const clbm_params* p, cudaStream_t s, void* buf_a, void* buf_b,
+                        clbm_ctx** out) {
+  if (!buf_a || !buf_b || !s) return CLBM_EINVAL;
+  return create_impl(p, s, buf_a, buf_b, out);
+}
+
+ViewInfo describe_view(const clbm_ctx* c) {
+  ViewInfo v;
+  v.g = make_geom(c);
+  v.c = make_coef(c);
+  v.buf[0] = c->buf[0];
+  v.buf[1] = c->buf[1];
+  v.pitch = c->pitch;
+  v.plane = c->plane;
+  v.bnodes_host = c->h_bnodes.data();
+  v.nb = (int)c->h_bnodes.size();
+  return v;
+}
+
+void set_view_time(clbm_ctx* c, int64_t t, int cur) {
+  c->t = t;
+  c->cur = cur;
+}
+
+}  // namespace clbm

@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "../../include/clbm.h"
+
 namespace clbm {
 
 // Node flag bits of the masked lattice layout (one uint16_t per node).
@@ -43,6 +45,8 @@ struct StepArgs {
   void* dst;        // post-collision state at time t + 1
   uint32_t seed;    // per-step key of the stochastic-rounding hash
   int stochastic;   // 16-bit stores: 0 = nearest even, 1 = stochastic
+  const int32_t* bnodes;  // boundary nodes (pitch-layout indices) recomputed after the interior
+  int nb;
 };
 
 // One Nusselt link, prepared on the host: node index (pitch layout) of x_f,
@@ -50,6 +54,26 @@ struct StepArgs {
 struct NuLink {
   long long own, second;
   double ne, b1, b2, b3;
+};
+
+// ---------------------------------------------------------------------------
+// Batched solves: many independent lattices advanced by the same launches.
+// ---------------------------------------------------------------------------
+constexpr int kBatchGroups = 3;  // tile width 32, 64, 128 nodes
+
+// One lattice of a batch as the batched kernels see it.
+struct BatchLat {
+  DevGeom g;
+  DevCoef c;
+  void* buf[2];  // this lattice's two distribution buffers inside the batch arena
+};
+
+// Device-resident control block of a batched solve.
+struct BatchCtl {
+  long long t;                 // steps taken since the solve started
+  int n_active;                // lattices still iterating
+  int pad;
+  int count[kBatchGroups];     // tiles per launch group
 };
 
 // Launchers implemented once per storage type (S = double, float, __half,
@@ -67,12 +91,43 @@ struct Launchers {
   cudaError_t (*nusselt)(const DevGeom& g, const DevCoef& c, const void* buf, const NuLink* links,
                          int nlinks, double* partials, int nblocks, cudaStream_t s);
   size_t elem_bytes;
+  // batched interior step over a tile list (tile = {lattice, row, first x, 0}); V = nodes per lane
+  cudaError_t (*batch_step)(int V, const BatchLat* lats, const int4* tiles, const int* count,
+                            int parity, const long long* t, int tstep, int stochastic, int grid,
+                            cudaStream_t s);
+  // batched boundary nodes: entries {lattice, node index}, skipped when the lattice is inactive
+  cudaError_t (*batch_boundary)(const BatchLat* lats, const int2* entries, int n, const int* active,
+                                int parity, const long long* t, int tstep, int stochastic,
+                                cudaStream_t s);
+  // persistent grid size (blocks) of the batched interior step for V
+  int (*batch_grid)(int V);
+  // per-lattice residual of buf[0] (current) against buf[1] (previous); +inf if non-finite
+  cudaError_t (*batch_residual)(const BatchLat* lats, const int* active, double* res, int n,
+                                cudaStream_t s);
 };
 
 extern const Launchers kLaunchF64;
 extern const Launchers kLaunchF32;
 extern const Launchers kLaunchF16;
 extern const Launchers kLaunchBF16;
+
+// Internal view API used by batches: a context whose two distribution buffers
+// belong to someone else (the batch arena).
+struct ViewInfo {
+  DevGeom g;
+  DevCoef c;
+  void* buf[2];
+  int pitch;
+  long long plane;
+  const int32_t* bnodes_host;  // boundary node list of the lattice (host copy)
+  int nb;
+};
+int view_pitch(int nx, int precision);
+size_t view_buffer_bytes(int nx, int ny, int precision);
+clbm_status create_view(const clbm_params* p, cudaStream_t s, void* buf_a, void* buf_b,
+                        clbm_ctx** out);
+ViewInfo describe_view(const clbm_ctx* c);
+void set_view_time(clbm_ctx* c, int64_t t, int cur);
 
 // Fixed-order sum of nblocks x width partials into out[width] (one block).
 cudaError_t launch_reduce_partials(const double* partials, int nblocks, int width, double* out,

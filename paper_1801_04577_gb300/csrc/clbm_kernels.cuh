@@ -41,6 +41,7 @@
 namespace clbm {
 
 constexpr int kStepThreads = 128;
+constexpr int kRedThreads = 256;
 
 // ---------------------------------------------------------------------------
 // Lattice (Eq. 3)
@@ -103,61 +104,46 @@ __device__ __forceinline__ __nv_bfloat16 from_r<__nv_bfloat16, float>(float v) {
   return __float2bfloat16_rn(v);
 }
 
-// Vector load / store of V consecutive elements (16-byte or 8-byte aligned).
-__device__ __forceinline__ void ldv(const double* p, double (&o)[2]) {
-  const double2 v = *reinterpret_cast<const double2*>(p);
-  o[0] = v.x;
-  o[1] = v.y;
-}
-__device__ __forceinline__ void ldv(const float* p, float (&o)[4]) {
-  const float4 v = *reinterpret_cast<const float4*>(p);
-  o[0] = v.x;
-  o[1] = v.y;
-  o[2] = v.z;
-  o[3] = v.w;
-}
-__device__ __forceinline__ void ldv(const __half* p, float (&o)[4]) {
-  const uint2 raw = *reinterpret_cast<const uint2*>(p);
-  __half2 a, b;
-  memcpy(&a, &raw.x, 4);
-  memcpy(&b, &raw.y, 4);
-  const float2 fa = __half22float2(a), fb = __half22float2(b);
-  o[0] = fa.x;
-  o[1] = fa.y;
-  o[2] = fb.x;
-  o[3] = fb.y;
-}
-__device__ __forceinline__ void ldv(const __nv_bfloat16* p, float (&o)[4]) {
-  const uint2 raw = *reinterpret_cast<const uint2*>(p);
-  __nv_bfloat162 a, b;
-  memcpy(&a, &raw.x, 4);
-  memcpy(&b, &raw.y, 4);
-  const float2 fa = __bfloat1622float2(a), fb = __bfloat1622float2(b);
-  o[0] = fa.x;
-  o[1] = fa.y;
-  o[2] = fb.x;
-  o[3] = fb.y;
+// Vector load / store of V consecutive elements as one naturally aligned
+// access of V * sizeof(S) bytes (2 to 16 bytes).
+template <int B>
+struct RawOf;
+template <>
+struct RawOf<2> {
+  using T = unsigned short;
+};
+template <>
+struct RawOf<4> {
+  using T = unsigned int;
+};
+template <>
+struct RawOf<8> {
+  using T = uint2;
+};
+template <>
+struct RawOf<16> {
+  using T = uint4;
+};
+
+template <typename S, int V, typename R>
+__device__ __forceinline__ void ldv(const S* p, R (&o)[V]) {
+  using Raw = typename RawOf<sizeof(S) * V>::T;
+  const Raw r = *reinterpret_cast<const Raw*>(p);
+  S e[V];
+  memcpy(e, &r, sizeof(Raw));
+#pragma unroll
+  for (int k = 0; k < V; ++k) o[k] = to_r(e[k]);
 }
 
-__device__ __forceinline__ void stv(double* p, const double (&o)[2]) {
-  *reinterpret_cast<double2*>(p) = make_double2(o[0], o[1]);
-}
-__device__ __forceinline__ void stv(float* p, const float (&o)[4]) {
-  *reinterpret_cast<float4*>(p) = make_float4(o[0], o[1], o[2], o[3]);
-}
-__device__ __forceinline__ void stv(__half* p, const float (&o)[4]) {
-  const __half2 a = __floats2half2_rn(o[0], o[1]), b = __floats2half2_rn(o[2], o[3]);
-  uint2 raw;
-  memcpy(&raw.x, &a, 4);
-  memcpy(&raw.y, &b, 4);
-  *reinterpret_cast<uint2*>(p) = raw;
-}
-__device__ __forceinline__ void stv(__nv_bfloat16* p, const float (&o)[4]) {
-  const __nv_bfloat162 a = __floats2bfloat162_rn(o[0], o[1]), b = __floats2bfloat162_rn(o[2], o[3]);
-  uint2 raw;
-  memcpy(&raw.x, &a, 4);
-  memcpy(&raw.y, &b, 4);
-  *reinterpret_cast<uint2*>(p) = raw;
+template <typename S, int V, typename R>
+__device__ __forceinline__ void stv(S* p, const R (&o)[V]) {
+  using Raw = typename RawOf<sizeof(S) * V>::T;
+  S e[V];
+#pragma unroll
+  for (int k = 0; k < V; ++k) e[k] = from_r<S, R>(o[k]);
+  Raw r;
+  memcpy(&r, e, sizeof(Raw));
+  *reinterpret_cast<Raw*>(p) = r;
 }
 
 // ---------------------------------------------------------------------------
@@ -190,18 +176,29 @@ __device__ __forceinline__ uint32_t cvt_rs_bf16x2(float lo, float hi, uint32_t r
   return d;
 }
 
-__device__ __forceinline__ void stv_sr(double* p, const double (&o)[2], uint32_t, uint32_t) {
-  stv(p, o);
+template <typename S>
+__device__ __forceinline__ uint32_t cvt_rs2(float lo, float hi, uint32_t r);
+template <>
+__device__ __forceinline__ uint32_t cvt_rs2<__half>(float lo, float hi, uint32_t r) {
+  return cvt_rs_f16x2(lo, hi, r);
 }
-__device__ __forceinline__ void stv_sr(float* p, const float (&o)[4], uint32_t, uint32_t) {
-  stv(p, o);
+template <>
+__device__ __forceinline__ uint32_t cvt_rs2<__nv_bfloat16>(float lo, float hi, uint32_t r) {
+  return cvt_rs_bf16x2(lo, hi, r);
 }
-__device__ __forceinline__ void stv_sr(__half* p, const float (&o)[4], uint32_t r0, uint32_t r1) {
-  *reinterpret_cast<uint2*>(p) = make_uint2(cvt_rs_f16x2(o[0], o[1], r0), cvt_rs_f16x2(o[2], o[3], r1));
-}
-__device__ __forceinline__ void stv_sr(__nv_bfloat16* p, const float (&o)[4], uint32_t r0,
-                                       uint32_t r1) {
-  *reinterpret_cast<uint2*>(p) = make_uint2(cvt_rs_bf16x2(o[0], o[1], r0), cvt_rs_bf16x2(o[2], o[3], r1));
+
+// Stochastically rounded store of V values (16-bit formats only).
+template <typename S, int V>
+__device__ __forceinline__ void stv_sr(S* p, const float (&o)[V], uint32_t r0, uint32_t r1) {
+  static_assert(sizeof(S) == 2, "stochastic rounding applies to 16-bit storage");
+  if constexpr (V == 1) {
+    *reinterpret_cast<unsigned short*>(p) = (unsigned short)(cvt_rs2<S>(o[0], 0.0f, r0) & 0xFFFFu);
+  } else if constexpr (V == 2) {
+    *reinterpret_cast<unsigned int*>(p) = cvt_rs2<S>(o[0], o[1], r0);
+  } else {
+    static_assert(V == 4, "16-bit tiles use 1, 2 or 4 nodes per lane");
+    *reinterpret_cast<uint2*>(p) = make_uint2(cvt_rs2<S>(o[0], o[1], r0), cvt_rs2<S>(o[2], o[3], r1));
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -391,9 +388,8 @@ __device__ __forceinline__ R node_T(const S* __restrict__ src, long long plane, 
 
 // Fix-up of one node that touches a wall, a periodic seam or a solid.
 template <typename S, bool MASK, typename R>
-__device__ __forceinline__ void fixup(const StepArgs& a, const Co<R>& c, const S* __restrict__ src,
+__device__ __forceinline__ void fixup(const DevGeom& g, const Co<R>& c, const S* __restrict__ src,
                                       int x, int y, uint16_t fl, R (&d)[9], R (&h)[5]) {
-  const DevGeom& g = a.g;
   const long long plane = g.plane;
   const long long own = (long long)y * g.pitch + x;
   const R T1 = node_T(src, plane, own, c);
@@ -459,27 +455,27 @@ __device__ __forceinline__ void fixup(const StepArgs& a, const Co<R>& c, const S
 // ---------------------------------------------------------------------------
 // The fused step kernel
 // ---------------------------------------------------------------------------
-template <typename S, bool MASK>
-__global__ void __launch_bounds__(kStepThreads) step_kernel(const StepArgs a) {
+// Interior update.  One warp updates the 32 * V nodes x = xw .. xw + 32V - 1
+// of row y (each lane owns V consecutive nodes); all 32 lanes must call it
+// together.  Every node is pulled and collided as if it were an interior
+// fluid node: rows beyond a non-periodic edge are clamped and the ±1 x-shift
+// at the row ends reads a neighbour, so box edges, periodic seams and nodes
+// next to solids come out wrong here and are recomputed afterwards by the
+// boundary kernel from its precomputed node list.  Keeping the walls out of
+// this kernel keeps its warps free of divergent wall code.
+template <typename S, int V>
+__device__ __forceinline__ void step_tile(const DevGeom& g, const Co<typename Traits<S>::R>& c,
+                                          const S* __restrict__ src, S* __restrict__ dst, int y,
+                                          int xw, int lane, uint32_t seed, int stochastic) {
   using R = typename Traits<S>::R;
-  constexpr int V = Traits<S>::V;
-  const DevGeom& g = a.g;
-  const int lane = threadIdx.x & 31;
-  const int warp = blockIdx.x * (kStepThreads / 32) + (threadIdx.x >> 5);
-  const int xw = warp * 32 * V;
-  if (xw >= g.nx) return;  // whole warps only: shuffles below need all 32 lanes
-  const int y = blockIdx.y;
   const int x0 = xw + lane * V;
   const long long plane = g.plane;
-  const S* __restrict__ src = static_cast<const S*>(a.src);
-  S* __restrict__ dst = static_cast<S*>(a.dst);
-  const Co<R> c = make_co<R>(a.c);
 
   int ym = y - 1, yp = y + 1;  // rows the e_y = +1 / -1 populations come from
   if (g.py) {
     ym = ym < 0 ? g.ny - 1 : ym;
     yp = yp >= g.ny ? 0 : yp;
-  } else {  // clamped rows are never used: the fix-up replaces those values
+  } else {
     ym = ym < 0 ? 0 : ym;
     yp = yp >= g.ny ? g.ny - 1 : yp;
   }
@@ -494,7 +490,7 @@ __global__ void __launch_bounds__(kStepThreads) step_kernel(const StepArgs a) {
     const int row = ey > 0 ? ym : (ey < 0 ? yp : y);
     const S* base = src + q * plane + (long long)row * g.pitch;
     R t[V];
-    ldv(base + x0, t);
+    ldv<S, V>(base + x0, t);
     if (ex == 0) {
 #pragma unroll
       for (int k = 0; k < V; ++k) v[q][k] = t[k];
@@ -513,36 +509,14 @@ __global__ void __launch_bounds__(kStepThreads) step_kernel(const StepArgs a) {
     }
   }
 
-  uint16_t fl[V];
-#pragma unroll
-  for (int k = 0; k < V; ++k) fl[k] = 0;
-  if (MASK) {
-    const uint16_t* fp = g.flags + (long long)y * g.pitch + x0;
-#pragma unroll
-    for (int k = 0; k < V; ++k) fl[k] = fp[k];
-  }
-  const bool yedge = !g.py && (y == 0 || y == g.ny - 1);
-
 #pragma unroll
   for (int k = 0; k < V; ++k) {
-    const int x = x0 + k;
     R d[9], h[5];
 #pragma unroll
     for (int q = 0; q < 9; ++q) d[q] = v[q][k];
 #pragma unroll
     for (int q = 0; q < 5; ++q) h[q] = v[9 + q][k];
-    bool active = x < g.nx;
-    if (MASK) active = active && !(fl[k] & kFlagSolid);
-    bool edge = yedge || x == 0 || x == g.nx - 1;
-    if (MASK) edge = edge || (fl[k] & 0xFFu);
-    if (active && edge) fixup<S, MASK>(a, c, src, x, y, fl[k], d, h);
     collide(c, d, h);
-    if (!active) {
-#pragma unroll
-      for (int q = 0; q < 9; ++q) d[q] = R(0);
-#pragma unroll
-      for (int q = 0; q < 5; ++q) h[q] = R(0);
-    }
 #pragma unroll
     for (int q = 0; q < 9; ++q) v[q][k] = d[q];
 #pragma unroll
@@ -550,18 +524,89 @@ __global__ void __launch_bounds__(kStepThreads) step_kernel(const StepArgs a) {
   }
 
   S* out = dst + (long long)y * g.pitch + x0;
-  if (sizeof(S) == 2 && a.stochastic) {
-    const uint32_t key = a.seed ^ mix32((uint32_t)((long long)y * g.pitch + x0));
+  if constexpr (sizeof(S) == 2) {
+    if (stochastic) {
+      const uint32_t key = seed ^ mix32((uint32_t)((long long)y * g.pitch + x0));
 #pragma unroll
-    for (int q = 0; q < 14; ++q) {
-      const uint32_t r0 = mix32(key + 0x9E3779B9u * (uint32_t)(q + 1));
-      const uint32_t r1 = mix32(r0 ^ 0x85EBCA6Bu);
-      stv_sr(out + q * plane, v[q], r0, r1);
+      for (int q = 0; q < 14; ++q) {
+        const uint32_t r0 = mix32(key + 0x9E3779B9u * (uint32_t)(q + 1));
+        const uint32_t r1 = mix32(r0 ^ 0x85EBCA6Bu);
+        stv_sr<S, V>(out + q * plane, v[q], r0, r1);
+      }
+      return;
     }
-  } else {
-#pragma unroll
-    for (int q = 0; q < 14; ++q) stv(out + q * plane, v[q]);
   }
+#pragma unroll
+  for (int q = 0; q < 14; ++q) stv<S, V>(out + q * plane, v[q]);
+}
+
+// Store of one value (stochastically rounded for 16-bit storage when asked).
+template <typename S, typename R>
+__device__ __forceinline__ void st1(S* p, R v, int stochastic, uint32_t r) {
+  if constexpr (sizeof(S) == 2) {
+    if (stochastic) {
+      *reinterpret_cast<unsigned short*>(p) = (unsigned short)(cvt_rs2<S>(v, 0.0f, r) & 0xFFFFu);
+      return;
+    }
+  }
+  *p = from_r<S, R>(v);
+}
+
+// Boundary update of node index i (pitch layout): pull with clamped indices,
+// then the fix-up applies bounce-back, Eq. 26-28 and periodic wrapping.
+template <typename S, bool MASK>
+__device__ __forceinline__ void step_node(const DevGeom& g, const Co<typename Traits<S>::R>& c,
+                                          const S* __restrict__ src, S* __restrict__ dst,
+                                          long long i, uint32_t seed, int stochastic) {
+  using R = typename Traits<S>::R;
+  const int y = (int)(i / g.pitch), x = (int)(i - (long long)y * g.pitch);
+  const long long plane = g.plane;
+  R d[9], h[5];
+#pragma unroll
+  for (int q = 0; q < 14; ++q) {
+    const int dir = q < 9 ? q : q - 9;
+    int sx = x - ex_of(dir), sy = y - ey_of(dir);
+    sx = sx < 0 ? 0 : (sx >= g.nx ? g.nx - 1 : sx);
+    sy = sy < 0 ? 0 : (sy >= g.ny ? g.ny - 1 : sy);
+    const R val = to_r(src[q * plane + (long long)sy * g.pitch + sx]);
+    if (q < 9)
+      d[q] = val;
+    else
+      h[q - 9] = val;
+  }
+  const uint16_t fl = MASK ? g.flags[i] : (uint16_t)0;
+  fixup<S, MASK>(g, c, src, x, y, fl, d, h);
+  collide(c, d, h);
+  const uint32_t key = seed ^ mix32((uint32_t)i);
+#pragma unroll
+  for (int q = 0; q < 14; ++q) {
+    const uint32_t r = mix32(key + 0x9E3779B9u * (uint32_t)(q + 1));
+    st1<S, R>(dst + q * plane + i, q < 9 ? d[q] : h[q - 9], stochastic, r);
+  }
+}
+
+// One launch = the interior update of one time step of one lattice.
+template <typename S>
+__global__ void __launch_bounds__(kStepThreads) step_kernel(const StepArgs a) {
+  using R = typename Traits<S>::R;
+  constexpr int V = Traits<S>::V;
+  const int lane = threadIdx.x & 31;
+  const int warp = blockIdx.x * (kStepThreads / 32) + (threadIdx.x >> 5);
+  const int xw = warp * 32 * V;
+  if (xw >= a.g.nx) return;  // whole warps only: the shuffles need all 32 lanes
+  const Co<R> c = make_co<R>(a.c);
+  step_tile<S, V>(a.g, c, static_cast<const S*>(a.src), static_cast<S*>(a.dst), blockIdx.y, xw,
+                  lane, a.seed, a.stochastic);
+}
+
+// The boundary nodes of the same step (launched after step_kernel).
+template <typename S, bool MASK>
+__global__ void __launch_bounds__(kRedThreads) boundary_kernel(const StepArgs a) {
+  using R = typename Traits<S>::R;
+  const Co<R> c = make_co<R>(a.c);
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < a.nb; k += gridDim.x * blockDim.x)
+    step_node<S, MASK>(a.g, c, static_cast<const S*>(a.src), static_cast<S*>(a.dst), a.bnodes[k],
+                       a.seed, a.stochastic);
 }
 
 // ---------------------------------------------------------------------------
@@ -648,7 +693,6 @@ __global__ void moments_kernel(const DevGeom g, const DevCoef c, const S* __rest
 // Deterministic FP64 reductions: each block writes its partial sums; a single
 // block adds the partials in index order.
 // ---------------------------------------------------------------------------
-constexpr int kRedThreads = 256;
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -719,6 +763,124 @@ __global__ void __launch_bounds__(kRedThreads)
 }
 
 // ---------------------------------------------------------------------------
+// Batched solves: the step kernel walks a tile list with a persistent grid
+// (each warp takes tiles w, w + #warps, ...), so the same launch serves any
+// number of active lattices; the list is rebuilt on the device as lattices
+// converge.
+// ---------------------------------------------------------------------------
+// Each warp takes one contiguous chunk of the tile list (tiles are ordered by
+// lattice, row, x), so it stays on one lattice for many tiles; the lattice's
+// descriptor is copied into a per-warp shared-memory slot when it changes and
+// read from there, instead of chasing it through global memory on every tile.
+template <typename S, int V>
+__global__ void __launch_bounds__(kStepThreads, 4)
+    batch_step_kernel(const BatchLat* __restrict__ lats, const int4* __restrict__ tiles,
+                      const int* __restrict__ count, int parity, const long long* __restrict__ tptr,
+                      int tstep, int stochastic) {
+  using R = typename Traits<S>::R;
+  static_assert(sizeof(BatchLat) % 8 == 0, "descriptor is copied in 8-byte words");
+  __shared__ BatchLat slot[kStepThreads / 32];
+  const int lane = threadIdx.x & 31;
+  const int wib = threadIdx.x >> 5;
+  const long long n = *count;
+  const long long nw = (long long)gridDim.x * (kStepThreads / 32);
+  const long long chunk = (n + nw - 1) / nw;
+  const long long begin = ((long long)blockIdx.x * (kStepThreads / 32) + wib) * chunk;
+  const long long end = begin + chunk < n ? begin + chunk : n;
+  uint32_t seed = 0;
+  if (stochastic) {
+    const long long t = *tptr + tstep;
+    seed = (uint32_t)(t * 0x9E3779B1ull) ^ (uint32_t)(t >> 32);
+  }
+  BatchLat& L = slot[wib];
+  int cur = -1;
+  Co<R> c;
+  for (long long w = begin; w < end; ++w) {
+    const int4 tl = tiles[w];
+    if (tl.x != cur) {
+      __syncwarp();
+      const unsigned long long* from = reinterpret_cast<const unsigned long long*>(lats + tl.x);
+      unsigned long long* to = reinterpret_cast<unsigned long long*>(&L);
+      for (int k = lane; k < (int)(sizeof(BatchLat) / 8); k += 32) to[k] = from[k];
+      __syncwarp();
+      cur = tl.x;
+      c = make_co<R>(L.c);
+    }
+    step_tile<S, V>(L.g, c, static_cast<const S*>(L.buf[parity]),
+                    static_cast<S*>(L.buf[parity ^ 1]), tl.y, tl.z, lane, seed, stochastic);
+  }
+}
+
+// Boundary nodes of every active lattice of a batch: entries {lattice, node}.
+template <typename S>
+__global__ void __launch_bounds__(kRedThreads)
+    batch_boundary_kernel(const BatchLat* __restrict__ lats, const int2* __restrict__ entries,
+                          int n, const int* __restrict__ active, int parity,
+                          const long long* __restrict__ tptr, int tstep, int stochastic) {
+  using R = typename Traits<S>::R;
+  uint32_t seed = 0;
+  if (stochastic) {
+    const long long t = *tptr + tstep;
+    seed = (uint32_t)(t * 0x9E3779B1ull) ^ (uint32_t)(t >> 32);
+  }
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    const int2 e = entries[k];
+    if (!active[e.x]) continue;
+    const BatchLat* L = lats + e.x;
+    const Co<R> c = make_co<R>(L->c);
+    const S* src = static_cast<const S*>(L->buf[parity]);
+    S* dst = static_cast<S*>(L->buf[parity ^ 1]);
+    if (L->g.flags)
+      step_node<S, true>(L->g, c, src, dst, e.y, seed, stochastic);
+    else
+      step_node<S, false>(L->g, c, src, dst, e.y, seed, stochastic);
+  }
+}
+
+// Residual of every active lattice, one block per lattice, FP64 in a fixed order.
+template <typename S>
+__global__ void __launch_bounds__(kRedThreads)
+    batch_residual_kernel(const BatchLat* __restrict__ lats, const int* __restrict__ active,
+                          double* __restrict__ res) {
+  const int i = blockIdx.x;
+  if (!active[i]) return;
+  const BatchLat* L = lats + i;
+  const DevGeom& g = L->g;
+  const S* cur = static_cast<const S*>(L->buf[0]);
+  const S* prev = static_cast<const S*>(L->buf[1]);
+  double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  const long long n = (long long)g.ny * g.nx;
+  for (long long k = threadIdx.x; k < n; k += blockDim.x) {
+    const int y = (int)(k / g.nx), x = (int)(k - (long long)y * g.nx);
+    const long long idx = (long long)y * g.pitch + x;
+    if (g.flags && (g.flags[idx] & kFlagSolid)) continue;
+    double r1, u1, v1, t1, r0, u0, v0, t0;
+    node_macros(L->c, cur, g.plane, idx, r1, u1, v1, t1);
+    node_macros(L->c, prev, g.plane, idx, r0, u0, v0, t0);
+    acc[0] += (t1 - t0) * (t1 - t0);
+    acc[1] += t1 * t1;
+    acc[2] += (u1 - u0) * (u1 - u0);
+    acc[3] += u1 * u1;
+    acc[4] += (v1 - v0) * (v1 - v0);
+    acc[5] += v1 * v1;
+    if (!isfinite(r1) || !isfinite(u1) || !isfinite(v1) || !isfinite(t1)) acc[6] += 1.0;
+  }
+  __shared__ double tot[8];
+  block_sum_store<8>(acc, tot);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double best = 0.0;
+    for (int q = 0; q < 3; ++q) {
+      const double den = sqrt(tot[2 * q + 1]) > 1e-30 ? sqrt(tot[2 * q + 1]) : 1e-30;
+      const double v = sqrt(tot[2 * q]) / den;
+      best = v > best ? v : best;
+    }
+    if (tot[6] != 0.0 || !isfinite(best)) best = INFINITY;
+    res[i] = best;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Launchers for one storage type
 // ---------------------------------------------------------------------------
 template <typename S>
@@ -728,10 +890,14 @@ struct LaunchImpl {
   static cudaError_t step(const StepArgs& a, cudaStream_t s) {
     const int nodes_per_block = kStepThreads * V;
     dim3 grid((a.g.nx + nodes_per_block - 1) / nodes_per_block, a.g.ny);
-    if (a.g.flags)
-      step_kernel<S, true><<<grid, kStepThreads, 0, s>>>(a);
-    else
-      step_kernel<S, false><<<grid, kStepThreads, 0, s>>>(a);
+    step_kernel<S><<<grid, kStepThreads, 0, s>>>(a);
+    if (a.nb > 0) {
+      const int blocks = (a.nb + kRedThreads - 1) / kRedThreads;
+      if (a.g.flags)
+        boundary_kernel<S, true><<<blocks, kRedThreads, 0, s>>>(a);
+      else
+        boundary_kernel<S, false><<<blocks, kRedThreads, 0, s>>>(a);
+    }
     return cudaGetLastError();
   }
 
@@ -772,8 +938,69 @@ struct LaunchImpl {
     return cudaGetLastError();
   }
 
+  template <int VV>
+  static cudaError_t batch_launch(const BatchLat* lats, const int4* tiles, const int* count,
+                                  int parity, const long long* t, int tstep, int stochastic, int grid,
+                                  cudaStream_t s) {
+    batch_step_kernel<S, VV><<<grid, kStepThreads, 0, s>>>(lats, tiles, count, parity, t, tstep,
+                                                            stochastic);
+    return cudaGetLastError();
+  }
+
+  static cudaError_t batch_step(int v, const BatchLat* lats, const int4* tiles, const int* count,
+                                int parity, const long long* t, int tstep, int stochastic, int grid,
+                                cudaStream_t s) {
+    if (v == 1) return batch_launch<1>(lats, tiles, count, parity, t, tstep, stochastic, grid, s);
+    if (v == 2) return batch_launch<2>(lats, tiles, count, parity, t, tstep, stochastic, grid, s);
+    if constexpr (V >= 4) {
+      if (v == 4) return batch_launch<4>(lats, tiles, count, parity, t, tstep, stochastic, grid, s);
+    }
+    return cudaErrorInvalidValue;
+  }
+
+  static cudaError_t batch_boundary(const BatchLat* lats, const int2* entries, int n,
+                                    const int* active, int parity, const long long* t, int tstep,
+                                    int stochastic, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    int blocks = (n + kRedThreads - 1) / kRedThreads;
+    if (blocks > 4096) blocks = 4096;
+    batch_boundary_kernel<S><<<blocks, kRedThreads, 0, s>>>(lats, entries, n, active, parity, t,
+                                                             tstep, stochastic);
+    return cudaGetLastError();
+  }
+
+  template <int VV>
+  static int grid_of() {
+    int per_sm = 0, dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_step_kernel<S, VV>,
+                                                      kStepThreads, 0) != cudaSuccess)
+      return 0;
+    return sms * (per_sm > 0 ? per_sm : 1);
+  }
+
+  static int batch_grid(int v) {
+    if (v == 1) return grid_of<1>();
+    if (v == 2) return grid_of<2>();
+    if constexpr (V >= 4) {
+      if (v == 4) return grid_of<4>();
+    }
+    return 0;
+  }
+
+  static cudaError_t batch_residual(const BatchLat* lats, const int* active, double* res, int n,
+                                    cudaStream_t s) {
+    batch_residual_kernel<S><<<n, kRedThreads, 0, s>>>(lats, active, res);
+    return cudaGetLastError();
+  }
+
   static Launchers table() {
     Launchers L;
+    L.batch_step = &batch_step;
+    L.batch_boundary = &batch_boundary;
+    L.batch_grid = &batch_grid;
+    L.batch_residual = &batch_residual;
     L.vec = V;
     L.step = &step;
     L.init = &init;

@@ -403,3 +403,60 @@ def fluid_count(w: Workload) -> int:
     if w.geom.solid is None:
         return w.params.nx * w.params.ny
     return int((w.geom.solid == 0).sum())
+
+
+BATCH_SEED = 1801045771
+
+
+def random_cavities(n: int = 512, seed: int = BATCH_SEED, hmin: int = 32, hmax: int = 512,
+                    U: float = 0.1) -> List[Workload]:
+    """Seeded batch of closed cavities of uneven size and physics.
+
+    Per cavity: H ~ U{hmin..hmax}, aspect a ~ U[1, 4], W = min(hmax, round(a H)),
+    orientation random (nx, ny) = (W, H) or (H, W); Ra log-uniform in
+    [1e3, 1e6]; Pr ~ U[0.7, 7]; Q = 0 with probability 1/2, else log-uniform
+    in [1e-6, 1e-4]; each side independently Dirichlet (T = 0 or 1), adiabatic
+    or Robin (b1 = 1, b2 = 1/H, b3 = T_amb/H, T_amb ~ U[0, 1]).  Draws with a
+    source and no wall that fixes the temperature level (b2 = 0 everywhere) are
+    rejected: they have no steady state.  Gravity along -y, the rates follow
+    Sec. 3.3 with the vertical size ny as H.
+    """
+    out = []
+    draw = 0
+    while len(out) < n:
+        r = splitmix64_uniform(seed + 7919 * draw, 16)
+        draw += 1
+        H = hmin + int(r[0] * (hmax - hmin + 1))
+        H = min(H, hmax)
+        a = 1.0 + 3.0 * r[1]
+        W = min(hmax, int(round(a * H)))
+        nx, ny = (W, H) if r[2] < 0.5 else (H, W)
+        Ra = 10.0 ** (3.0 + 3.0 * r[3])
+        Pr = 0.7 + 6.3 * r[4]
+        Q = 0.0 if r[5] < 0.5 else 10.0 ** (-6.0 + 2.0 * r[6])
+        tbc, side = [], []
+        fixes_level = False
+        dirichlet_T = []
+        for s in range(4):
+            kind = min(2, int(3 * r[7 + s]))
+            if kind == 0:
+                Tw = 1.0 if r[11 + s] < 0.5 else 0.0
+                tbc.append(dirichlet(Tw))
+                dirichlet_T.append(Tw)
+                fixes_level = True
+            elif kind == 1:
+                tbc.append(neumann(0.0))
+            else:
+                tbc.append(robin(1.0, 1.0 / ny, r[11 + s] / ny))
+                fixes_level = True
+            side.append(s)
+        if Q > 0 and not fixes_level:
+            continue
+        nu, alpha, s_nu, lambda1, gbeta = convection_rates(ny, Ra, Pr, U, 1.0)
+        T0 = float(np.mean(dirichlet_T)) if dirichlet_T else 0.5
+        p = Params(nx=nx, ny=ny, s_nu=s_nu, lambda1=lambda1, T0=T0, gbeta=gbeta, Q=Q)
+        g = Geometry(tbc=tbc, side_tbc=tuple(side))
+        w = Workload(f"cavity{len(out)}_{nx}x{ny}_Ra{Ra:.3g}_Pr{Pr:.3g}", p, g,
+                     Fields(T=np.full((ny, nx), T0)), length=float(ny), dT=1.0, u_scale=U)
+        out.append(w)
+    return out

@@ -1,0 +1,90 @@
+"""Batched solves (many lattices per launch) against single-lattice runs and the oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1801_04577_gb300 import clbm
+from paper_1801_04577_gb300 import inputs as I
+
+from _parity import TOL, compare
+
+pytestmark = pytest.mark.gpu
+
+
+def mixed_workloads():
+    return [I.obstacle_channel(), I.natural_convection_cavity(48, 1e4),
+            I.rayleigh_benard(300, 70, Ra=1e5, Q=1e-4, noise=1e-2), I.diffusion_channel(0.1, nx=4),
+            I.periodic_box(133, 37), I.annulus(64, 2.6, Ra=1e4),
+            I.natural_convection_cavity(20, 1e3)]
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+@pytest.mark.parametrize("autotune", [False, True])
+def test_batch_matches_single_lattice_runs(precision, autotune):
+    """tol = 0: no lattice retires, so every lattice takes exactly max_steps steps
+    and must reproduce its own single-lattice run."""
+    ws = mixed_workloads()
+    b = clbm.Batch(ws, precision, autotune=autotune)
+    conv, res, steps = b.solve(0.0, 200, check_every=100)
+    assert steps == 200
+    assert (conv == -1).all()
+    for i, w in enumerate(ws):
+        s = clbm.from_workload(w, precision)
+        s.step(200)
+        ref = s.moments()
+        got = b.moments(i)
+        errs = compare(w, got, ref)
+        assert max(errs.values()) <= (1e-13 if precision == "f64" else 1e-6), (i, w.name, errs)
+        assert b.tile_width(i) in (32, 64, 128)
+    b.close()
+
+
+def test_batch_against_oracle_f64():
+    ws = mixed_workloads()[:3]
+    b = clbm.Batch(ws, "f64")
+    b.solve(0.0, 300, check_every=150)
+    for i, w in enumerate(ws):
+        o = oracle.from_workload(w)
+        o.step(300)
+        errs = compare(w, b.moments(i), o.moments())
+        assert max(errs.values()) <= TOL["f64"], (w.name, errs)
+    b.close()
+
+
+def test_batch_convergence_and_retirement():
+    """Cavities reach the tolerance at different times; each converged lattice
+    stops at its own step count with its residual below tol.  (The per-step
+    residual of a closed cavity levels off at a small floor that shrinks with
+    the size -- about 1e-6 at 16^2, 5e-8 at 32^2 in the oracle too -- so the
+    cases are 32^2 and larger.)"""
+    ws = [I.natural_convection_cavity(H, Ra) for H, Ra in ((32, 1e3), (40, 1e3), (32, 1e4))]
+    ws[2].params.lambda1 = 1.0 / (0.12 / 0.4 + 0.5)
+    b = clbm.Batch(ws, "f64")
+    tol = 2e-7
+    conv, res, steps = b.solve(tol, 40000, check_every=50)
+    assert (conv > 0).all(), conv
+    assert (res < tol).all()
+    assert steps == conv.max()
+    for i, w in enumerate(ws):
+        v = b.view(i)
+        assert clbm.clbm_time(v) == conv[i]
+        # the frozen state is the single-lattice state after the same number of steps
+        s = clbm.from_workload(w, "f64")
+        s.step(int(conv[i]))
+        errs = compare(w, b.moments(i), s.moments())
+        assert max(errs.values()) <= 1e-13
+        assert clbm.clbm_residual(v) == pytest.approx(res[i], rel=1e-9)
+    b.close()
+
+
+def test_batch_flags_diverged_lattice():
+    ws = [I.natural_convection_cavity(24, 1e3), I.obstacle_channel()]
+    T = np.full((24, 24), 0.5)
+    T[3, 4] = np.nan
+    ws[0].init = I.Fields(T=T)
+    b = clbm.Batch(ws, "f32")
+    conv, res, steps = b.solve(1e-30, 400, check_every=100)
+    assert conv[0] == -2 and not np.isfinite(res[0])
+    assert conv[1] == -1 and np.isfinite(res[1])
+    assert steps == 400
+    b.close()

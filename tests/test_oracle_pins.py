@@ -401,3 +401,17 @@ def test_invalid_descriptions_rejected():
     w.geom.link_tbc = w.geom.link_tbc[1:]
     with pytest.raises(ValueError):
         oracle.from_workload(w)
+
+
+def test_random_cavity_generator_properties():
+    """The seeded batch generator: sizes, stable rates, and no source without a
+    wall that fixes the temperature level."""
+    ws = I.random_cavities(64)
+    assert len(ws) == 64
+    assert ws[0].params.nx == I.random_cavities(1)[0].params.nx  # deterministic
+    for w in ws:
+        p = w.params
+        assert 32 <= min(p.nx, p.ny) and max(p.nx, p.ny) <= 512
+        assert 0 < p.s_nu < 2 and 0 < p.lambda1 < 2
+        if p.Q > 0:
+            assert any(t[1] != 0 for t in w.geom.tbc)
