@@ -225,10 +225,15 @@ typedef struct {
 clbm_status clbm_batch_create(const clbm_batch_item* items, int32_t n, int32_t autotune,
                               void* stream, clbm_batch** out);
 
-/* Advance every lattice until its steady-state residual (the clbm_residual
- * quantity, checked every check_every steps, rounded up to an even number)
- * falls below tol, or until max_steps steps (the last check may overrun by
- * less than check_every).  Each check_every block of steps is one replay of a
+/* Advance every lattice until its steady-state residual falls below tol, or
+ * until max_steps steps (the last check may overrun by less than
+ * check_every).  The residual is checked every K = check_every steps
+ * (rounded up to an even number) as max over phi in {T, ux, uy} of
+ * ||phi(t) - phi(t - K)||_2 / (K ||phi(t)||_2) over fluid nodes: the mean
+ * per-step change over the interval.  Comparing states an even number of
+ * steps apart ignores the small period-2 oscillation that closed cavities can
+ * sustain, which keeps the one-step quantity of clbm_residual above tight
+ * tolerances.  The first check of a solve only takes the snapshot.  Each check_every block of steps is one replay of a
  * captured CUDA graph; converged lattices leave the device-side work list.
  * Outputs (host arrays of n, may be NULL): conv_steps[i] = step count at
  * which lattice i converged, -1 if it did not, -2 if it diverged (NaN/Inf);
@@ -249,6 +254,50 @@ clbm_status clbm_batch_destroy(clbm_batch* b);
 
 /* Message of the last failure on this batch ("" if none). */
 const char* clbm_batch_last_error(const clbm_batch* b);
+
+/* ---------------------------------------------------------------------
+ * Surrogate network for warm starts (no counterpart in the paper): a
+ * convolutional encoder-decoder (U-Net) on a G x G grid, trained and run
+ * by the library's own kernels (implicit-GEMM convolutions, FP32
+ * accumulation, BF16 weights with an FP32 master copy, Adam).
+ *   levels L (2..6), base width B: widths B, 2B, ..., 2^(L-1) B; G must be
+ *   divisible by 2^(L-1).  Input in_ch, output out_ch channels (NCHW FP32).
+ * All tensors passed to these calls are FP32 device arrays.
+ * ------------------------------------------------------------------- */
+typedef struct clbm_net clbm_net;
+
+typedef struct {
+  int32_t grid, in_ch, out_ch, base, levels, max_batch;
+} clbm_net_config;
+
+/* Create a network with seeded He-uniform weights and zero biases. */
+clbm_status clbm_net_create(const clbm_net_config* cfg, uint64_t seed, void* stream, clbm_net** out);
+
+/* Number of parameters (weights and biases of every layer, in layer order;
+ * each layer: weights [co][ci][k][k] then bias [co]). */
+clbm_status clbm_net_param_count(const clbm_net* net, int64_t* count);
+
+/* Copy the FP32 master parameters out / in (host or device array).  Setting
+ * parameters also refreshes the BF16 copy and resets the Adam state. */
+clbm_status clbm_net_get_params(const clbm_net* net, float* dst, int32_t on_device);
+clbm_status clbm_net_set_params(clbm_net* net, const float* src, int32_t on_device);
+
+/* y[N][out_ch][G][G] = net(x[N][in_ch][G][G]), 1 <= N <= max_batch (async). */
+clbm_status clbm_net_forward(clbm_net* net, const float* x, int32_t n, float* y);
+
+/* Loss and parameter gradients: loss = sum mask (y - t)^2 / (sum mask * out_ch)
+ * with mask[N][G][G] (NULL = all ones).  grad (param_count floats, host or
+ * device, may be NULL) receives dloss/dparams; *loss (may be NULL) the loss.
+ * Synchronises. */
+clbm_status clbm_net_gradients(clbm_net* net, const float* x, const float* target,
+                               const float* mask, int32_t n, float* grad, double* loss);
+
+/* clbm_net_gradients followed by one Adam step (beta 0.9, 0.999, eps 1e-8). */
+clbm_status clbm_net_train_step(clbm_net* net, const float* x, const float* target,
+                                const float* mask, int32_t n, float lr, double* loss);
+
+clbm_status clbm_net_destroy(clbm_net* net);
+const char* clbm_net_last_error(const clbm_net* net);
 
 /* Number of time steps taken since the last initialisation. */
 clbm_status clbm_time(const clbm_ctx* ctx, int64_t* t_out);

@@ -117,6 +117,8 @@ struct clbm_batch {
   int4* d_tiles = nullptr;
   long long tile_cap = 0;
   int4** d_group_tiles = nullptr;
+  double* d_snap = nullptr;  // convergence snapshots of all lattices
+  int* d_snap_valid = nullptr;
   int2* d_bent = nullptr;  // boundary entries {lattice, node} of all lattices
   int nbent = 0;
   cudaGraphExec_t exec = nullptr;
@@ -219,6 +221,8 @@ static void release(clbm_batch* b) {
   cudaFree(b->d_tiles);
   cudaFree(b->d_group_tiles);
   cudaFree(b->d_bent);
+  cudaFree(b->d_snap);
+  cudaFree(b->d_snap_valid);
   if (b->h_ctl) cudaFreeHost(b->h_ctl);
   if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
 }
@@ -347,8 +351,16 @@ clbm_status clbm_batch_create(const clbm_batch_item* items, int32_t n, int32_t a
   }
   if (cap >= (1LL << 31)) return bail(CLBM_EINVAL);
   // device tables
+  long long snap_total = 0;
+  for (int i = 0; i < n; ++i) snap_total += 3 * b->nodes[i];
+  if (cudaMalloc(&b->d_snap, snap_total * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&b->d_snap_valid, n * sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    return bail(CLBM_ENOMEM);
+  }
   std::vector<BatchLat> lats(n);
   std::vector<int2> bent;
+  long long snap_off = 0;
   b->masked.assign(n, 0);
   for (int i = 0; i < n; ++i) {
     const ViewInfo v = describe_view(b->views[i]);
@@ -356,6 +368,8 @@ clbm_status clbm_batch_create(const clbm_batch_item* items, int32_t n, int32_t a
     lats[i].c = v.c;
     lats[i].buf[0] = v.buf[0];
     lats[i].buf[1] = v.buf[1];
+    lats[i].snap = b->d_snap + snap_off;
+    snap_off += 3 * b->nodes[i];
     b->masked[i] = v.g.flags != nullptr;
     for (int k = 0; k < v.nb; ++k) bent.push_back(make_int2(i, v.bnodes_host[k]));
   }
@@ -424,6 +438,7 @@ clbm_status clbm_batch_solve(clbm_batch* b, double tol, int64_t max_steps, int32
   std::vector<long long> minus1(n, -1);
   BCUDA(b, cudaMemcpyAsync(b->d_conv, minus1.data(), n * sizeof(long long), cudaMemcpyHostToDevice, b->stream));
   BCUDA(b, cudaMemsetAsync(b->d_ctl, 0, sizeof(BatchCtl), b->stream));
+  BCUDA(b, cudaMemsetAsync(b->d_snap_valid, 0, n * sizeof(int), b->stream));
   for (int i = 0; i < n; ++i) set_view_time(b->views[i], 0, 0);
   if ((st = build_tiles(b)) != CLBM_OK) return st;
   if (!b->exec || b->exec_K != K || b->exec_tol != tol) {
@@ -435,7 +450,8 @@ clbm_status clbm_batch_solve(clbm_batch* b, double tol, int64_t max_steps, int32
     BCUDA(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
     clbm_status cst = CLBM_OK;
     for (int j = 0; j < K && cst == CLBM_OK; ++j) cst = launch_steps(b, j & 1, j);
-    if (cst == CLBM_OK && b->L->batch_residual(b->d_lats, b->d_active, b->d_res, n, b->stream) != cudaSuccess)
+    if (cst == CLBM_OK && b->L->batch_residual(b->d_lats, b->d_active, b->d_snap_valid, b->d_res, n, K,
+                                               b->stream) != cudaSuccess)
       cst = CLBM_ECUDA;
     if (cst == CLBM_OK) {
       batch_update_kernel<<<1, 256, 0, b->stream>>>(n, b->d_active, b->d_res, tol, b->d_conv, b->d_ctl, K);

@@ -66,6 +66,7 @@ struct BatchLat {
   DevGeom g;
   DevCoef c;
   void* buf[2];  // this lattice's two distribution buffers inside the batch arena
+  double* snap;  // (T, ux, uy) at the previous convergence check, dense [3][ny][nx]
 };
 
 // Device-resident control block of a batched solve.
@@ -101,9 +102,10 @@ struct Launchers {
                                 cudaStream_t s);
   // persistent grid size (blocks) of the batched interior step for V
   int (*batch_grid)(int V);
-  // per-lattice residual of buf[0] (current) against buf[1] (previous); +inf if non-finite
-  cudaError_t (*batch_residual)(const BatchLat* lats, const int* active, double* res, int n,
-                                cudaStream_t s);
+  // per-lattice residual: change of (T, ux, uy) since the previous check (snapshot), per step
+  // (divided by K); 1e300 when there is no snapshot yet, +inf if a value is non-finite
+  cudaError_t (*batch_residual)(const BatchLat* lats, const int* active, int* snap_valid,
+                                double* res, int n, int K, cudaStream_t s);
 };
 
 extern const Launchers kLaunchF64;

@@ -837,26 +837,32 @@ __global__ void __launch_bounds__(kRedThreads)
   }
 }
 
-// Residual of every active lattice, one block per lattice, FP64 in a fixed order.
+// Convergence measure of every active lattice, one block per lattice, FP64 in
+// a fixed order: max over (T, ux, uy) of ||phi(t) - phi(t - K)||_2 /
+// (K ||phi(t)||_2), against the snapshot taken at the previous check, which is
+// then replaced.  Comparing states K (even) steps apart is blind to the
+// period-2 oscillation a closed cavity can keep at a small amplitude, which
+// would otherwise hold a one-step residual above the tolerance.
 template <typename S>
 __global__ void __launch_bounds__(kRedThreads)
     batch_residual_kernel(const BatchLat* __restrict__ lats, const int* __restrict__ active,
-                          double* __restrict__ res) {
+                          int* __restrict__ snap_valid, double* __restrict__ res, int K) {
   const int i = blockIdx.x;
   if (!active[i]) return;
   const BatchLat* L = lats + i;
   const DevGeom& g = L->g;
   const S* cur = static_cast<const S*>(L->buf[0]);
-  const S* prev = static_cast<const S*>(L->buf[1]);
-  double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   const long long n = (long long)g.ny * g.nx;
+  double* snap = L->snap;
+  const bool have = snap_valid[i] != 0;
+  double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   for (long long k = threadIdx.x; k < n; k += blockDim.x) {
     const int y = (int)(k / g.nx), x = (int)(k - (long long)y * g.nx);
     const long long idx = (long long)y * g.pitch + x;
     if (g.flags && (g.flags[idx] & kFlagSolid)) continue;
-    double r1, u1, v1, t1, r0, u0, v0, t0;
+    double r1, u1, v1, t1;
     node_macros(L->c, cur, g.plane, idx, r1, u1, v1, t1);
-    node_macros(L->c, prev, g.plane, idx, r0, u0, v0, t0);
+    const double t0 = snap[k], u0 = snap[n + k], v0 = snap[2 * n + k];
     acc[0] += (t1 - t0) * (t1 - t0);
     acc[1] += t1 * t1;
     acc[2] += (u1 - u0) * (u1 - u0);
@@ -864,6 +870,9 @@ __global__ void __launch_bounds__(kRedThreads)
     acc[4] += (v1 - v0) * (v1 - v0);
     acc[5] += v1 * v1;
     if (!isfinite(r1) || !isfinite(u1) || !isfinite(v1) || !isfinite(t1)) acc[6] += 1.0;
+    snap[k] = t1;
+    snap[n + k] = u1;
+    snap[2 * n + k] = v1;
   }
   __shared__ double tot[8];
   block_sum_store<8>(acc, tot);
@@ -875,8 +884,11 @@ __global__ void __launch_bounds__(kRedThreads)
       const double v = sqrt(tot[2 * q]) / den;
       best = v > best ? v : best;
     }
+    best /= (double)K;
+    if (!have) best = 1e300;
     if (tot[6] != 0.0 || !isfinite(best)) best = INFINITY;
     res[i] = best;
+    snap_valid[i] = 1;
   }
 }
 
@@ -989,9 +1001,9 @@ struct LaunchImpl {
     return 0;
   }
 
-  static cudaError_t batch_residual(const BatchLat* lats, const int* active, double* res, int n,
-                                    cudaStream_t s) {
-    batch_residual_kernel<S><<<n, kRedThreads, 0, s>>>(lats, active, res);
+  static cudaError_t batch_residual(const BatchLat* lats, const int* active, int* snap_valid,
+                                    double* res, int n, int K, cudaStream_t s) {
+    batch_residual_kernel<S><<<n, kRedThreads, 0, s>>>(lats, active, snap_valid, res, K);
     return cudaGetLastError();
   }
 

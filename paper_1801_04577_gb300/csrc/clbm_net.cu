@@ -1,0 +1,775 @@
+// Surrogate network for warm starts: a small convolutional encoder-decoder
+// (U-Net) mapping problem descriptors on a G x G grid to steady T, ux, uy,
+// trained and evaluated entirely by the kernels in this file.
+//
+// Layers (L levels, base width B, widths c_l = B 2^l):
+//   encoder l = 0..L-2 : conv3x3 + ReLU, conv3x3 + ReLU (= skip_l), 2x2 average pool
+//   bottleneck L-1     : conv3x3 + ReLU, conv3x3 + ReLU
+//   decoder l = L-2..0 : nearest 2x upsample, concat [up, skip_l], conv3x3 + ReLU, conv3x3 + ReLU
+//   head               : conv1x1 (no activation)
+// Activations are FP32 NCHW; weights are kept as an FP32 master copy (Adam)
+// and a BF16 copy that every convolution reads; accumulation is FP32.
+//
+// Every convolution pass is one implicit GEMM (gemm_kernel) with on-the-fly
+// im2col loaders:
+//   forward      Y[co, p]      = sum_{ci,t} W[co, ci t] X[ci, p + t]
+//   input grad   dX[ci, p]    += sum_{co,t} W'[ci, co t] dY[co, p + t]   (W' = W flipped, transposed)
+//   weight grad  dW[co, ci t]  = sum_p dY[co, p] X[ci, p + t]          (split-K over pixels,
+//                                                                       partials summed in order)
+// so the training step is deterministic.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <type_traits>
+#include <string>
+#include <vector>
+
+#include "../../include/clbm.h"
+
+namespace {
+
+constexpr int BM = 64, BN = 64, BK = 16, GT = 256;
+
+// ---------------------------------------------------------------------------
+// Loaders (element (m, k) of A, (k, n) of B) and stores for the GEMM
+// ---------------------------------------------------------------------------
+struct Act {  // one activation tensor view: sample n, channel c at base + n*cs*HW + (coff + c)*HW
+  const float* base;
+  int cs, coff, C, H, W;
+  __device__ __forceinline__ float at(int n, int c, int y, int x) const {
+    if (y < 0 || y >= H || x < 0 || x >= W) return 0.0f;
+    return base[((long long)n * cs + coff + c) * H * W + (long long)y * W + x];
+  }
+};
+
+// A(m, k) = weights[m][k] (BF16, row-major M x K)
+struct LoadW {
+  const __nv_bfloat16* w;
+  int K;
+  __device__ __forceinline__ float operator()(int m, int k) const {
+    return __bfloat162float(w[(long long)m * K + k]);
+  }
+};
+
+// B(k, n) = im2col(X): k = (c, tap), n = pixel (sample, y, x); ks = 1 or 3
+struct LoadIm2col {
+  Act x;
+  int ks;
+  __device__ __forceinline__ float operator()(int k, int n) const {
+    const int hw = x.H * x.W;
+    const int t = k % (ks * ks), c = k / (ks * ks);
+    const int nb = n / hw, p = n - nb * hw;
+    const int y = p / x.W, xx = p - y * x.W;
+    const int r = ks / 2;
+    return x.at(nb, c, y + t / ks - r, xx + t % ks - r);
+  }
+};
+
+// A(m, k) = act[sample][m][pixel]: m = channel, k = pixel (for weight gradients)
+struct LoadActMK {
+  Act a;
+  __device__ __forceinline__ float operator()(int m, int k) const {
+    const int hw = a.H * a.W;
+    const int nb = k / hw, p = k - nb * hw;
+    return a.base[((long long)nb * a.cs + a.coff + m) * hw + p];
+  }
+};
+
+// B(k, n) = im2col(X) transposed: k = pixel, n = (c, tap)
+struct LoadIm2colT {
+  Act x;
+  int ks;
+  __device__ __forceinline__ float operator()(int k, int n) const {
+    const int hw = x.H * x.W;
+    const int t = n % (ks * ks), c = n / (ks * ks);
+    const int nb = k / hw, p = k - nb * hw;
+    const int y = p / x.W, xx = p - y * x.W;
+    const int r = ks / 2;
+    return x.at(nb, c, y + t / ks - r, xx + t % ks - r);
+  }
+};
+
+// C(m = channel, n = pixel) into an activation view, with bias / ReLU / accumulate.
+struct StoreAct {
+  float* base;
+  int cs, coff, H, W;
+  const float* bias;
+  int relu, accumulate;
+  __device__ __forceinline__ void operator()(int m, int n, float v) const {
+    const int hw = H * W;
+    const int nb = n / hw, p = n - nb * hw;
+    float* dst = base + ((long long)nb * cs + coff + m) * hw + p;
+    if (bias) v += bias[m];
+    if (relu) v = v > 0.0f ? v : 0.0f;
+    if (accumulate) v += *dst;
+    *dst = v;
+  }
+};
+
+// C(m, n) into a dense partial buffer: part[split][m][n]
+struct StorePartial {
+  float* part;
+  int M, N;
+  __device__ __forceinline__ void operator()(int m, int n, float v, int split) const {
+    part[((long long)split * M + m) * N + n] = v;
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Tiled FP32 GEMM: 64 x 64 output tile per block, 4 x 4 per thread, K in
+// chunks of 16 staged in shared memory.  blockIdx.z = K split.
+// ---------------------------------------------------------------------------
+template <class LA, class LB, class ST>
+__global__ void __launch_bounds__(GT) gemm_kernel(LA la, LB lb, ST st, int M, int N, int K,
+                                                  int kper) {
+  __shared__ float As[BK][BM + 4];
+  __shared__ float Bs[BK][BN + 4];
+  const int tid = threadIdx.x;
+  const int tx = tid % 16, ty = tid / 16;
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  const int kbeg = blockIdx.z * kper;
+  const int kend = min(K, kbeg + kper);
+  float acc[4][4] = {};
+  for (int k0 = kbeg; k0 < kend; k0 += BK) {
+#pragma unroll
+    for (int r = 0; r < (BK * BM) / GT; ++r) {
+      const int e = tid + r * GT;
+      const int kk = e / BM, mm = e % BM;
+      const int m = m0 + mm, k = k0 + kk;
+      As[kk][mm] = (m < M && k < kend) ? la(m, k) : 0.0f;
+    }
+#pragma unroll
+    for (int r = 0; r < (BK * BN) / GT; ++r) {
+      const int e = tid + r * GT;
+      const int kk = e / BN, nn = e % BN;
+      const int n = n0 + nn, k = k0 + kk;
+      Bs[kk][nn] = (n < N && k < kend) ? lb(k, n) : 0.0f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      float a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx * 4 + j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int m = m0 + ty * 4 + i, n = n0 + tx * 4 + j;
+      if (m < M && n < N) {
+        if constexpr (std::is_same<ST, StorePartial>::value)
+          st(m, n, acc[i][j], blockIdx.z);
+        else
+          st(m, n, acc[i][j]);
+      }
+    }
+}
+
+// out[i] = sum_s part[s][i] (fixed order); optional accumulate
+__global__ void sum_splits_kernel(const float* __restrict__ part, int splits, long long n,
+                                  float* __restrict__ out) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    float s = 0.0f;
+    for (int k = 0; k < splits; ++k) s += part[(long long)k * n + i];
+    out[i] = s;
+  }
+}
+
+// db[c] = sum over samples and pixels of g[n][c][p] (one block per channel, fixed order)
+__global__ void bias_grad_kernel(Act g, int N, float* __restrict__ db) {
+  __shared__ float sh[GT];
+  const int c = blockIdx.x;
+  const int hw = g.H * g.W;
+  float s = 0.0f;
+  for (long long k = threadIdx.x; k < (long long)N * hw; k += blockDim.x) {
+    const int nb = (int)(k / hw), p = (int)(k - (long long)nb * hw);
+    s += g.base[((long long)nb * g.cs + g.coff + c) * hw + p];
+  }
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = GT / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) db[c] = sh[0];
+}
+
+// g *= (y > 0) over one activation view (ReLU backward, in place on g)
+__global__ void relu_back_kernel(Act y, float* __restrict__ g, int gcs, int gcoff, int N) {
+  const long long hw = (long long)y.H * y.W, tot = (long long)N * y.C * hw;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int nb = (int)(i / (y.C * hw));
+    const long long r = i - (long long)nb * y.C * hw;
+    const int c = (int)(r / hw);
+    const long long p = r - (long long)c * hw;
+    const float yv = y.base[((long long)nb * y.cs + y.coff + c) * hw + p];
+    float* gp = g + ((long long)nb * gcs + gcoff + c) * hw + p;
+    if (!(yv > 0.0f)) *gp = 0.0f;
+  }
+}
+
+// 2x2 average pool: out (H/2 x W/2) from in; backward adds g_out/4 to the four inputs
+__global__ void pool_kernel(Act in, float* __restrict__ out, int ocs, int ocoff, int N) {
+  const int Ho = in.H / 2, Wo = in.W / 2;
+  const long long tot = (long long)N * in.C * Ho * Wo;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(i % Wo), y = (int)((i / Wo) % Ho), c = (int)((i / ((long long)Wo * Ho)) % in.C);
+    const int nb = (int)(i / ((long long)Wo * Ho * in.C));
+    const float s = in.at(nb, c, 2 * y, 2 * x) + in.at(nb, c, 2 * y, 2 * x + 1) +
+                    in.at(nb, c, 2 * y + 1, 2 * x) + in.at(nb, c, 2 * y + 1, 2 * x + 1);
+    out[((long long)nb * ocs + ocoff + c) * Ho * Wo + (long long)y * Wo + x] = 0.25f * s;
+  }
+}
+__global__ void pool_back_kernel(Act gout, float* __restrict__ gin, int gcs, int gcoff, int N) {
+  const int H = gout.H * 2, W = gout.W * 2;
+  const long long tot = (long long)N * gout.C * H * W;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(i % W), y = (int)((i / W) % H), c = (int)((i / ((long long)W * H)) % gout.C);
+    const int nb = (int)(i / ((long long)W * H * gout.C));
+    gin[((long long)nb * gcs + gcoff + c) * H * W + (long long)y * W + x] +=
+        0.25f * gout.at(nb, c, y / 2, x / 2);
+  }
+}
+
+// nearest 2x upsample; backward sums the four outputs of each input
+__global__ void up_kernel(Act in, float* __restrict__ out, int ocs, int ocoff, int N) {
+  const int H = in.H * 2, W = in.W * 2;
+  const long long tot = (long long)N * in.C * H * W;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(i % W), y = (int)((i / W) % H), c = (int)((i / ((long long)W * H)) % in.C);
+    const int nb = (int)(i / ((long long)W * H * in.C));
+    out[((long long)nb * ocs + ocoff + c) * H * W + (long long)y * W + x] = in.at(nb, c, y / 2, x / 2);
+  }
+}
+__global__ void up_back_kernel(Act gout, float* __restrict__ gin, int gcs, int gcoff, int N) {
+  const int Hi = gout.H / 2, Wi = gout.W / 2;
+  const long long tot = (long long)N * gout.C * Hi * Wi;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(i % Wi), y = (int)((i / Wi) % Hi), c = (int)((i / ((long long)Wi * Hi)) % gout.C);
+    const int nb = (int)(i / ((long long)Wi * Hi * gout.C));
+    const float s = gout.at(nb, c, 2 * y, 2 * x) + gout.at(nb, c, 2 * y, 2 * x + 1) +
+                    gout.at(nb, c, 2 * y + 1, 2 * x) + gout.at(nb, c, 2 * y + 1, 2 * x + 1);
+    gin[((long long)nb * gcs + gcoff + c) * Hi * Wi + (long long)y * Wi + x] += s;
+  }
+}
+
+// masked MSE: loss = sum mask (y - t)^2 / (sum mask * C); g = dloss/dy.  One block
+// per sample writes FP64 partials (fixed order), summed on the host.
+__global__ void loss_kernel(const float* __restrict__ y, const float* __restrict__ t,
+                            const float* __restrict__ mask, int C, int HW, double inv_norm,
+                            float* __restrict__ g, double* __restrict__ part) {
+  __shared__ double sh[GT];
+  const int nb = blockIdx.x;
+  double s = 0.0;
+  for (int k = threadIdx.x; k < C * HW; k += blockDim.x) {
+    const int c = k / HW, p = k - c * HW;
+    const long long i = ((long long)nb * C + c) * HW + p;
+    const double w = mask ? mask[(long long)nb * HW + p] : 1.0;
+    const double d = (double)y[i] - (double)t[i];
+    s += w * d * d;
+    g[i] = (float)(2.0 * w * d * inv_norm);
+  }
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = GT / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[nb] = sh[0];
+}
+
+// Adam on the FP32 master parameters, refreshing the BF16 copy.
+__global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ g,
+                            float* __restrict__ m, float* __restrict__ v,
+                            __nv_bfloat16* __restrict__ pb, long long n, float lr, float b1,
+                            float b2, float eps, float c1, float c2) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.0f - b1) * gi;
+    const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    const float pi = p[i] - lr * (mi * c1) / (sqrtf(vi * c2) + eps);
+    p[i] = pi;
+    pb[i] = __float2bfloat16_rn(pi);
+  }
+}
+
+__global__ void to_bf16_kernel(const float* __restrict__ p, __nv_bfloat16* __restrict__ pb, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    pb[i] = __float2bfloat16_rn(p[i]);
+}
+
+// W'[ci][co t'] = W[co][ci t] with t' = flipped tap (for input gradients)
+__global__ void flip_kernel(const __nv_bfloat16* __restrict__ w, __nv_bfloat16* __restrict__ wt,
+                            int Co, int Ci, int ks) {
+  const int kk = ks * ks;
+  const long long tot = (long long)Co * Ci * kk;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int t = (int)(i % kk), ci = (int)((i / kk) % Ci), co = (int)(i / ((long long)kk * Ci));
+    wt[((long long)ci * Co + co) * kk + (kk - 1 - t)] = w[i];
+  }
+}
+
+int grid1(long long n) {
+  long long b = (n + 255) / 256;
+  return (int)(b < 1 ? 1 : (b > 8192 ? 8192 : b));
+}
+
+struct Conv {  // one convolution layer
+  int ci, co, ks, H, W;
+  long long w_off, b_off;  // offsets in the parameter vector (weights, then bias)
+};
+
+// activation buffers of the U-Net, in forward order
+enum { kMaxLevels = 6 };
+
+struct Plan {
+  // buffer ids
+  int in, a1[kMaxLevels], cat[kMaxLevels], pool[kMaxLevels], b1, b2, d1[kMaxLevels], d2[kMaxLevels], out;
+};
+
+}  // namespace
+
+struct clbm_net {
+  clbm_net_config cfg{};
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::vector<Conv> convs;
+  long long nparam = 0;
+  float *p = nullptr, *g = nullptr, *m = nullptr, *v = nullptr;
+  __nv_bfloat16 *pb = nullptr, *pt = nullptr;  // BF16 weights and flipped copy
+  std::vector<float*> act, gact;               // per buffer
+  std::vector<int> act_c, act_hw;              // channels and H (= W) of each buffer
+  float* part = nullptr;                       // split-K partials
+  long long part_cap = 0;
+  double* loss_part = nullptr;
+  int64_t steps = 0;
+  Plan plan{};
+  std::string err;
+};
+
+namespace {
+
+Plan make_plan(clbm_net* net) {
+  const int L = net->cfg.levels, B = net->cfg.base, G = net->cfg.grid;
+  Plan P;
+  auto add = [&](int c, int h) {
+    net->act_c.push_back(c);
+    net->act_hw.push_back(h);
+    return (int)net->act_c.size() - 1;
+  };
+  P.in = add(net->cfg.in_ch, G);
+  for (int l = 0; l < L - 1; ++l) {
+    const int c = B << l, h = G >> l;
+    P.a1[l] = add(c, h);
+    P.cat[l] = add((B << (l + 1)) + c, h);  // [up (c_{l+1}) | skip (c_l)]
+    P.pool[l] = add(c, h / 2);
+  }
+  const int cb = B << (L - 1), hb = G >> (L - 1);
+  P.b1 = add(cb, hb);
+  P.b2 = add(cb, hb);
+  for (int l = L - 2; l >= 0; --l) {
+    const int c = B << l, h = G >> l;
+    P.d1[l] = add(c, h);
+    P.d2[l] = add(c, h);
+  }
+  P.out = add(net->cfg.out_ch, G);
+  return P;
+}
+
+Act view(clbm_net* net, int id, int coff, int C, bool grad = false) {
+  Act a;
+  a.base = grad ? net->gact[id] : net->act[id];
+  a.cs = net->act_c[id];
+  a.coff = coff;
+  a.C = C;
+  a.H = a.W = net->act_hw[id];
+  return a;
+}
+
+cudaError_t conv_forward(clbm_net* net, const Conv& cv, Act x, int out_id, int out_coff, int relu,
+                         int N) {
+  const int M = cv.co, Kd = cv.ci * cv.ks * cv.ks, Np = N * cv.H * cv.W;
+  LoadW la{net->pb + cv.w_off, Kd};
+  LoadIm2col lb{x, cv.ks};
+  StoreAct st{net->act[out_id], net->act_c[out_id], out_coff, cv.H, cv.W, net->p + cv.b_off, relu, 0};
+  dim3 grid((Np + BN - 1) / BN, (M + BM - 1) / BM, 1);
+  gemm_kernel<<<grid, GT, 0, net->stream>>>(la, lb, st, M, Np, Kd, Kd);
+  return cudaGetLastError();
+}
+
+// Backward of y = act(conv(x)): gy is the gradient buffer of y (ReLU already applied
+// by the caller); accumulates into gx (if gx_id >= 0), writes dW, db.
+cudaError_t conv_backward(clbm_net* net, const Conv& cv, Act x, Act gy, int gx_id, int gx_coff,
+                          int N) {
+  const int Kd = cv.ci * cv.ks * cv.ks, Np = N * cv.H * cv.W;
+  // weight gradient: M = co, N = ci*t, K = pixels, split-K
+  {
+    const int kper = 4096;
+    const int splits = (Np + kper - 1) / kper;
+    const long long need = (long long)splits * cv.co * Kd;
+    if (need > net->part_cap) return cudaErrorInvalidValue;
+    LoadActMK la{gy};
+    LoadIm2colT lb{x, cv.ks};
+    StorePartial st{net->part, cv.co, Kd};
+    dim3 grid((Kd + BN - 1) / BN, (cv.co + BM - 1) / BM, splits);
+    gemm_kernel<<<grid, GT, 0, net->stream>>>(la, lb, st, cv.co, Kd, Np, kper);
+    const long long n = (long long)cv.co * Kd;
+    sum_splits_kernel<<<grid1(n), 256, 0, net->stream>>>(net->part, splits, n, net->g + cv.w_off);
+    bias_grad_kernel<<<cv.co, GT, 0, net->stream>>>(gy, N, net->g + cv.b_off);
+  }
+  if (gx_id >= 0) {  // input gradient: M = ci, N = pixels, K = co*t, with flipped weights
+    const int kk = cv.ks * cv.ks;
+    flip_kernel<<<grid1((long long)cv.co * cv.ci * kk), 256, 0, net->stream>>>(
+        net->pb + cv.w_off, net->pt + cv.w_off, cv.co, cv.ci, cv.ks);
+    LoadW la{net->pt + cv.w_off, cv.co * kk};
+    LoadIm2col lb{gy, cv.ks};
+    StoreAct st{net->gact[gx_id], net->act_c[gx_id], gx_coff, cv.H, cv.W, nullptr, 0, 1};
+    dim3 grid((Np + BN - 1) / BN, (cv.ci + BM - 1) / BM, 1);
+    gemm_kernel<<<grid, GT, 0, net->stream>>>(la, lb, st, cv.ci, Np, cv.co * kk, cv.co * kk);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t relu_back(clbm_net* net, int id, int coff, int C, int N) {
+  Act y = view(net, id, coff, C);
+  relu_back_kernel<<<grid1((long long)N * C * y.H * y.W), 256, 0, net->stream>>>(
+      y, net->gact[id], net->act_c[id], coff, N);
+  return cudaGetLastError();
+}
+
+// Full forward pass over N samples already in act[in].
+cudaError_t forward(clbm_net* net, const Plan& P, int N) {
+  const int L = net->cfg.levels, B = net->cfg.base;
+  cudaError_t e;
+  int ci = 0;
+  Act x = view(net, P.in, 0, net->cfg.in_ch);
+  for (int l = 0; l < L - 1; ++l) {
+    const int c = B << l, cup = B << (l + 1);
+    if ((e = conv_forward(net, net->convs[ci++], x, P.a1[l], 0, 1, N))) return e;
+    if ((e = conv_forward(net, net->convs[ci++], view(net, P.a1[l], 0, c), P.cat[l], cup, 1, N))) return e;
+    Act skip = view(net, P.cat[l], cup, c);
+    pool_kernel<<<grid1((long long)N * c * (skip.H / 2) * (skip.W / 2)), 256, 0, net->stream>>>(
+        skip, net->act[P.pool[l]], c, 0, N);
+    x = view(net, P.pool[l], 0, c);
+  }
+  const int cb = B << (L - 1);
+  if ((e = conv_forward(net, net->convs[ci++], x, P.b1, 0, 1, N))) return e;
+  if ((e = conv_forward(net, net->convs[ci++], view(net, P.b1, 0, cb), P.b2, 0, 1, N))) return e;
+  Act prev = view(net, P.b2, 0, cb);
+  for (int l = L - 2; l >= 0; --l) {
+    const int c = B << l, cup = B << (l + 1);
+    up_kernel<<<grid1((long long)N * cup * (prev.H * 2) * (prev.W * 2)), 256, 0, net->stream>>>(
+        prev, net->act[P.cat[l]], net->act_c[P.cat[l]], 0, N);
+    if ((e = conv_forward(net, net->convs[ci++], view(net, P.cat[l], 0, cup + c), P.d1[l], 0, 1, N))) return e;
+    if ((e = conv_forward(net, net->convs[ci++], view(net, P.d1[l], 0, c), P.d2[l], 0, 1, N))) return e;
+    prev = view(net, P.d2[l], 0, c);
+  }
+  if ((e = conv_forward(net, net->convs[ci++], prev, P.out, 0, 0, N))) return e;
+  return cudaGetLastError();
+}
+
+// Backward pass; gact[out] holds dloss/dout on entry; writes net->g.
+cudaError_t backward(clbm_net* net, const Plan& P, int N) {
+  const int L = net->cfg.levels, B = net->cfg.base;
+  cudaError_t e;
+  // zero all activation gradients except the output's
+  for (size_t id = 0; id + 1 < net->gact.size(); ++id) {
+    const long long n = (long long)N * net->act_c[id] * net->act_hw[id] * net->act_hw[id];
+    if ((e = cudaMemsetAsync(net->gact[id], 0, n * sizeof(float), net->stream))) return e;
+  }
+  int ci = (int)net->convs.size() - 1;
+  // head
+  {
+    const Conv& cv = net->convs[ci--];
+    if ((e = conv_backward(net, cv, view(net, P.d2[0], 0, B), view(net, P.out, 0, net->cfg.out_ch, true),
+                           P.d2[0], 0, N))) return e;
+  }
+  // decoder, shallowest level first (reverse of the forward order)
+  for (int l = 0; l <= L - 2; ++l) {
+    const int c = B << l, cup = B << (l + 1);
+    const Conv& c2 = net->convs[ci--];
+    const Conv& c1 = net->convs[ci--];
+    if ((e = relu_back(net, P.d2[l], 0, c, N))) return e;
+    if ((e = conv_backward(net, c2, view(net, P.d1[l], 0, c), view(net, P.d2[l], 0, c, true), P.d1[l], 0, N))) return e;
+    if ((e = relu_back(net, P.d1[l], 0, c, N))) return e;
+    if ((e = conv_backward(net, c1, view(net, P.cat[l], 0, cup + c), view(net, P.d1[l], 0, c, true), P.cat[l], 0, N))) return e;
+    // gradient of the upsampled part flows to the level below (d2[l+1] or b2)
+    const int below = (l + 1 <= L - 2) ? P.d2[l + 1] : P.b2;
+    Act gup = view(net, P.cat[l], 0, cup, true);
+    up_back_kernel<<<grid1((long long)N * cup * (gup.H / 2) * (gup.W / 2)), 256, 0, net->stream>>>(
+        gup, net->gact[below], net->act_c[below], 0, N);
+  }
+  // bottleneck
+  {
+    const int cb = B << (L - 1);
+    const Conv& c2 = net->convs[ci--];
+    const Conv& c1 = net->convs[ci--];
+    if ((e = relu_back(net, P.b2, 0, cb, N))) return e;
+    if ((e = conv_backward(net, c2, view(net, P.b1, 0, cb), view(net, P.b2, 0, cb, true), P.b1, 0, N))) return e;
+    if ((e = relu_back(net, P.b1, 0, cb, N))) return e;
+    const int inb = P.pool[L - 2];
+    if ((e = conv_backward(net, c1, view(net, inb, 0, B << (L - 2)), view(net, P.b1, 0, cb, true),
+                           inb, 0, N))) return e;
+  }
+  // encoder, deepest first
+  for (int l = L - 2; l >= 0; --l) {
+    const int c = B << l, cup = B << (l + 1);
+    const Conv& c2 = net->convs[ci--];
+    const Conv& c1 = net->convs[ci--];
+    // pool backward adds into the skip part of cat[l]
+    Act gp = view(net, P.pool[l], 0, c, true);
+    pool_back_kernel<<<grid1((long long)N * c * gp.H * 2 * gp.W * 2), 256, 0, net->stream>>>(
+        gp, net->gact[P.cat[l]], net->act_c[P.cat[l]], cup, N);
+    if ((e = relu_back(net, P.cat[l], cup, c, N))) return e;
+    if ((e = conv_backward(net, c2, view(net, P.a1[l], 0, c), view(net, P.cat[l], cup, c, true), P.a1[l], 0, N))) return e;
+    if ((e = relu_back(net, P.a1[l], 0, c, N))) return e;
+    const int inb = l > 0 ? P.pool[l - 1] : P.in;
+    const int cin = l > 0 ? (B << (l - 1)) : net->cfg.in_ch;
+    if ((e = conv_backward(net, c1, view(net, inb, 0, cin), view(net, P.a1[l], 0, c, true),
+                           l > 0 ? inb : -1, 0, N))) return e;
+  }
+  return cudaGetLastError();
+}
+
+clbm_status nfail(clbm_net* n, clbm_status s, const std::string& m) {
+  if (n) n->err = m;
+  return s;
+}
+
+clbm_status cuda_status(clbm_net* n, cudaError_t e, const char* where) {
+  if (e == cudaSuccess) return CLBM_OK;
+  return nfail(n, CLBM_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+// splitmix64 -> uniform [0, 1)
+double u01(uint64_t& s) {
+  s += 0x9E3779B97F4A7C15ull;
+  uint64_t z = s;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  z ^= z >> 31;
+  return (double)(z >> 11) * (1.0 / 9007199254740992.0);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* clbm_net_last_error(const clbm_net* n) { return n ? n->err.c_str() : ""; }
+
+clbm_status clbm_net_destroy(clbm_net* n) {
+  if (!n) return CLBM_OK;
+  if (n->stream) cudaStreamSynchronize(n->stream);
+  cudaFree(n->p);
+  cudaFree(n->g);
+  cudaFree(n->m);
+  cudaFree(n->v);
+  cudaFree(n->pb);
+  cudaFree(n->pt);
+  for (float* a : n->act) cudaFree(a);
+  for (float* a : n->gact) cudaFree(a);
+  cudaFree(n->part);
+  cudaFree(n->loss_part);
+  if (n->own_stream && n->stream) cudaStreamDestroy(n->stream);
+  delete n;
+  return CLBM_OK;
+}
+
+clbm_status clbm_net_create(const clbm_net_config* cfg, uint64_t seed, void* stream, clbm_net** out) {
+  if (!out || !cfg) return CLBM_EINVAL;
+  *out = nullptr;
+  const clbm_net_config& c = *cfg;
+  if (c.levels < 2 || c.levels > kMaxLevels || c.base < 1 || c.in_ch < 1 || c.out_ch < 1 ||
+      c.max_batch < 1 || c.grid < 2 || (c.grid % (1 << (c.levels - 1))) != 0)
+    return CLBM_EINVAL;
+  clbm_net* n = new (std::nothrow) clbm_net();
+  if (!n) return CLBM_ENOMEM;
+  n->cfg = c;
+  auto bail = [&](clbm_status s) {
+    clbm_net_destroy(n);
+    return s;
+  };
+  if (stream) {
+    n->stream = static_cast<cudaStream_t>(stream);
+  } else {
+    if (cudaStreamCreateWithFlags(&n->stream, cudaStreamNonBlocking) != cudaSuccess) return bail(CLBM_ECUDA);
+    n->own_stream = true;
+  }
+  // layers in forward order
+  const int L = c.levels, B = c.base, G = c.grid;
+  long long off = 0;
+  auto add_conv = [&](int ci, int co, int ks, int h) {
+    Conv cv{ci, co, ks, h, h, off, off + (long long)co * ci * ks * ks};
+    off = cv.b_off + co;
+    n->convs.push_back(cv);
+  };
+  for (int l = 0; l < L - 1; ++l) {
+    const int cin = l == 0 ? c.in_ch : (B << (l - 1));
+    add_conv(cin, B << l, 3, G >> l);
+    add_conv(B << l, B << l, 3, G >> l);
+  }
+  add_conv(B << (L - 2), B << (L - 1), 3, G >> (L - 1));
+  add_conv(B << (L - 1), B << (L - 1), 3, G >> (L - 1));
+  for (int l = L - 2; l >= 0; --l) {
+    add_conv((B << (l + 1)) + (B << l), B << l, 3, G >> l);
+    add_conv(B << l, B << l, 3, G >> l);
+  }
+  add_conv(B, c.out_ch, 1, G);
+  n->nparam = off;
+  // parameters: uniform(+-sqrt(6/fan_in)) weights (He), zero biases
+  std::vector<float> h((size_t)off, 0.0f);
+  uint64_t s = seed;
+  for (const Conv& cv : n->convs) {
+    const double a = std::sqrt(6.0 / (cv.ci * cv.ks * cv.ks));
+    for (long long k = 0; k < (long long)cv.co * cv.ci * cv.ks * cv.ks; ++k)
+      h[cv.w_off + k] = (float)((2.0 * u01(s) - 1.0) * a);
+  }
+  if (cudaMalloc(&n->p, off * sizeof(float)) || cudaMalloc(&n->g, off * sizeof(float)) ||
+      cudaMalloc(&n->m, off * sizeof(float)) || cudaMalloc(&n->v, off * sizeof(float)) ||
+      cudaMalloc(&n->pb, off * sizeof(__nv_bfloat16)) || cudaMalloc(&n->pt, off * sizeof(__nv_bfloat16)))
+    return bail(CLBM_ENOMEM);
+  cudaMemcpy(n->p, h.data(), off * sizeof(float), cudaMemcpyHostToDevice);
+  cudaMemset(n->m, 0, off * sizeof(float));
+  cudaMemset(n->v, 0, off * sizeof(float));
+  cudaMemset(n->g, 0, off * sizeof(float));
+  to_bf16_kernel<<<grid1(off), 256, 0, n->stream>>>(n->p, n->pb, off);
+  // activations
+  n->plan = make_plan(n);
+  for (size_t id = 0; id < n->act_c.size(); ++id) {
+    const long long e = (long long)c.max_batch * n->act_c[id] * n->act_hw[id] * n->act_hw[id];
+    float *a = nullptr, *ga = nullptr;
+    if (cudaMalloc(&a, e * sizeof(float)) || cudaMalloc(&ga, e * sizeof(float))) {
+      cudaFree(a);
+      return bail(CLBM_ENOMEM);
+    }
+    n->act.push_back(a);
+    n->gact.push_back(ga);
+  }
+  long long cap = 0;
+  for (const Conv& cv : n->convs) {
+    const long long splits = ((long long)c.max_batch * cv.H * cv.W + 4095) / 4096;
+    cap = std::max(cap, splits * cv.co * cv.ci * cv.ks * cv.ks);
+  }
+  n->part_cap = cap;
+  if (cudaMalloc(&n->part, cap * sizeof(float)) || cudaMalloc(&n->loss_part, c.max_batch * sizeof(double)))
+    return bail(CLBM_ENOMEM);
+  if (cudaStreamSynchronize(n->stream) != cudaSuccess) return bail(CLBM_ECUDA);
+  *out = n;
+  return CLBM_OK;
+}
+
+clbm_status clbm_net_param_count(const clbm_net* n, int64_t* count) {
+  if (!n || !count) return CLBM_EINVAL;
+  *count = n->nparam;
+  return CLBM_OK;
+}
+
+clbm_status clbm_net_get_params(const clbm_net* n, float* dst, int32_t on_device) {
+  if (!n || !dst) return CLBM_EINVAL;
+  if (cudaStreamSynchronize(n->stream)) return CLBM_ECUDA;
+  return cudaMemcpy(dst, n->p, n->nparam * sizeof(float),
+                    on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost) ? CLBM_ECUDA : CLBM_OK;
+}
+
+clbm_status clbm_net_set_params(clbm_net* n, const float* src, int32_t on_device) {
+  if (!n || !src) return CLBM_EINVAL;
+  if (cudaStreamSynchronize(n->stream) ||
+      cudaMemcpy(n->p, src, n->nparam * sizeof(float),
+                 on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice))
+    return CLBM_ECUDA;
+  to_bf16_kernel<<<grid1(n->nparam), 256, 0, n->stream>>>(n->p, n->pb, n->nparam);
+  cudaMemsetAsync(n->m, 0, n->nparam * sizeof(float), n->stream);
+  cudaMemsetAsync(n->v, 0, n->nparam * sizeof(float), n->stream);
+  n->steps = 0;
+  return cuda_status(n, cudaStreamSynchronize(n->stream), "set_params");
+}
+
+clbm_status clbm_net_forward(clbm_net* n, const float* x, int32_t N, float* y) {
+  if (!n || !x || !y || N < 1 || N > n->cfg.max_batch) return CLBM_EINVAL;
+  const Plan& P = n->plan;
+  const long long in_e = (long long)N * n->cfg.in_ch * n->cfg.grid * n->cfg.grid;
+  const long long out_e = (long long)N * n->cfg.out_ch * n->cfg.grid * n->cfg.grid;
+  cudaError_t e = cudaMemcpyAsync(n->act[P.in], x, in_e * sizeof(float), cudaMemcpyDeviceToDevice, n->stream);
+  if (!e) e = forward(n, P, N);
+  if (!e) e = cudaMemcpyAsync(y, n->act[P.out], out_e * sizeof(float), cudaMemcpyDeviceToDevice, n->stream);
+  return cuda_status(n, e, "forward");
+}
+
+clbm_status clbm_net_gradients(clbm_net* n, const float* x, const float* target, const float* mask,
+                               int32_t N, float* grad, double* loss) {
+  if (!n || !x || !target || N < 1 || N > n->cfg.max_batch) return CLBM_EINVAL;
+  const Plan& P = n->plan;
+  const int G = n->cfg.grid, C = n->cfg.out_ch;
+  const long long in_e = (long long)N * n->cfg.in_ch * G * G;
+  cudaError_t e = cudaMemcpyAsync(n->act[P.in], x, in_e * sizeof(float), cudaMemcpyDeviceToDevice, n->stream);
+  if (!e) e = forward(n, P, N);
+  // loss normalisation: sum of mask weights times channels
+  double norm = 0.0;
+  if (mask) {
+    std::vector<float> hm((size_t)N * G * G);
+    if (!e) e = cudaMemcpyAsync(hm.data(), mask, hm.size() * sizeof(float), cudaMemcpyDeviceToHost, n->stream);
+    if (!e) e = cudaStreamSynchronize(n->stream);
+    for (float w : hm) norm += w;
+  } else {
+    norm = (double)N * G * G;
+  }
+  norm *= C;
+  if (!(norm > 0)) return nfail(n, CLBM_EINVAL, "empty loss mask");
+  if (!e) {
+    loss_kernel<<<N, GT, 0, n->stream>>>(n->act[P.out], target, mask, C, G * G, 1.0 / norm,
+                                         n->gact[P.out], n->loss_part);
+    e = cudaGetLastError();
+  }
+  if (!e) e = backward(n, P, N);
+  std::vector<double> lp(N);
+  if (!e) e = cudaMemcpyAsync(lp.data(), n->loss_part, N * sizeof(double), cudaMemcpyDeviceToHost, n->stream);
+  if (!e) e = cudaStreamSynchronize(n->stream);
+  if (e) return cuda_status(n, e, "gradients");
+  double s = 0.0;
+  for (double v : lp) s += v;
+  if (loss) *loss = s / norm;
+  if (grad) {
+    e = cudaMemcpy(grad, n->g, n->nparam * sizeof(float), cudaMemcpyDefault);
+    if (e) return cuda_status(n, e, "copy gradients");
+  }
+  return CLBM_OK;
+}
+
+clbm_status clbm_net_train_step(clbm_net* n, const float* x, const float* target, const float* mask,
+                                int32_t N, float lr, double* loss) {
+  clbm_status st = clbm_net_gradients(n, x, target, mask, N, nullptr, loss);
+  if (st != CLBM_OK) return st;
+  n->steps += 1;
+  const float b1 = 0.9f, b2 = 0.999f;
+  const float c1 = 1.0f / (1.0f - std::pow(b1, (float)n->steps));
+  const float c2 = 1.0f / (1.0f - std::pow(b2, (float)n->steps));
+  adam_kernel<<<grid1(n->nparam), 256, 0, n->stream>>>(n->p, n->g, n->m, n->v, n->pb, n->nparam, lr,
+                                                        b1, b2, 1e-8f, c1, c2);
+  return cuda_status(n, cudaGetLastError(), "adam");
+}
+
+}  // extern "C"

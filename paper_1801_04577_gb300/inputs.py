@@ -460,3 +460,47 @@ def random_cavities(n: int = 512, seed: int = BATCH_SEED, hmin: int = 32, hmax: 
                      Fields(T=np.full((ny, nx), T0)), length=float(ny), dT=1.0, u_scale=U)
         out.append(w)
     return out
+
+
+SURROGATE_SEED = 1801045772
+
+
+def obstacle_cavities(n: int, G: int = 64, seed: int = SURROGATE_SEED, ra_range=(1e3, 1e5),
+                      max_obstacles: int = 2, U: float = 0.1) -> List[Workload]:
+    """Seeded differentially heated cavities with rectangular obstacles.
+
+    G x G fluid box, left wall T = 1, right wall T = 0, top and bottom
+    adiabatic, no-slip everywhere; 0..max_obstacles adiabatic rectangles with
+    sides in [G/16, G/4] kept at least two nodes away from the walls; Ra
+    log-uniform in ra_range, Pr ~ U[0.7, 7], Q = 0 with probability 1/2, else
+    log-uniform in [1e-6, 1e-4].  Rest start at T = 0.5.
+    """
+    out = []
+    for k in range(n):
+        r = splitmix64_uniform(seed + 104729 * k, 24)
+        lo, hi = np.log10(ra_range[0]), np.log10(ra_range[1])
+        Ra = 10.0 ** (lo + (hi - lo) * r[0])
+        Pr = 0.7 + 6.3 * r[1]
+        Q = 0.0 if r[2] < 0.5 else 10.0 ** (-6.0 + 2.0 * r[3])
+        nob = min(max_obstacles, int(r[4] * (max_obstacles + 1)))
+        solid = np.zeros((G, G), np.uint8)
+        smin, smax = max(2, G // 16), max(3, G // 4)
+        for o in range(nob):
+            w = smin + int(r[5 + 4 * o] * (smax - smin + 1))
+            h = smin + int(r[6 + 4 * o] * (smax - smin + 1))
+            x0 = 2 + int(r[7 + 4 * o] * (G - 4 - w))
+            y0 = 2 + int(r[8 + 4 * o] * (G - 4 - h))
+            solid[y0:y0 + h, x0:x0 + w] = 1
+        nu, alpha, s_nu, lambda1, gbeta = convection_rates(G, Ra, Pr, U, 1.0)
+        p = Params(nx=G, ny=G, s_nu=s_nu, lambda1=lambda1, T0=0.5, gbeta=gbeta, Q=Q)
+        tbc = [dirichlet(1.0), dirichlet(0.0), neumann(0.0)]
+        if solid.any():
+            ln, ld, le, lt = axis_links(solid, 2)
+            g = Geometry(tbc=tbc, side_tbc=(0, 1, 2, 2), solid=solid, link_node=ln, link_dir=ld,
+                         link_ne=le, link_tbc=lt)
+        else:
+            g = Geometry(tbc=tbc, side_tbc=(0, 1, 2, 2))
+        out.append(Workload(f"obstacle_cavity{k}_G{G}_Ra{Ra:.3g}", p, g, Fields(T=np.full((G, G), 0.5)),
+                            length=float(G), dT=1.0, u_scale=U))
+        out[-1].Ra, out[-1].Pr = Ra, Pr
+    return out

@@ -65,6 +65,7 @@ def test_batch_convergence_and_retirement():
     assert (conv > 0).all(), conv
     assert (res < tol).all()
     assert steps == conv.max()
+    assert (conv % 50 == 0).all() and (conv >= 100).all()  # the first check only takes a snapshot
     for i, w in enumerate(ws):
         v = b.view(i)
         assert clbm.clbm_time(v) == conv[i]
@@ -73,7 +74,6 @@ def test_batch_convergence_and_retirement():
         s.step(int(conv[i]))
         errs = compare(w, b.moments(i), s.moments())
         assert max(errs.values()) <= 1e-13
-        assert clbm.clbm_residual(v) == pytest.approx(res[i], rel=1e-9)
     b.close()
 
 
@@ -85,6 +85,6 @@ def test_batch_flags_diverged_lattice():
     b = clbm.Batch(ws, "f32")
     conv, res, steps = b.solve(1e-30, 400, check_every=100)
     assert conv[0] == -2 and not np.isfinite(res[0])
-    assert conv[1] == -1 and np.isfinite(res[1])
+    assert conv[1] == -1 and np.isfinite(res[1]) and res[1] < 1.0
     assert steps == 400
     b.close()
