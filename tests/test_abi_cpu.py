@@ -7,7 +7,7 @@ import re
 
 import pytest
 
-from paper_1801_04577_gb300 import build, clbm
+from paper_1801_04577_gb300 import build, clbm, net
 from paper_1801_04577_gb300 import inputs as I
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -26,7 +26,18 @@ def test_library_builds_and_exports_all_declared_symbols():
     assert len(names) >= 10
     for name in names:
         assert hasattr(lib, name), name
-    assert set(names) == set(clbm.EXPORTS)
+    assert set(names) == set(clbm.EXPORTS) | set(net.NET_EXPORTS)
+
+
+def test_net_create_rejects_bad_config():
+    L = net.load()
+    import ctypes as C
+    h = C.c_void_p()
+    for cfg in [(30, 5, 3, 8, 3, 4),   # grid not divisible by 2^(levels-1)
+                (32, 5, 3, 8, 1, 4),   # too few levels
+                (32, 0, 3, 8, 3, 4)]:  # no input channels
+        c = net.clbm_net_config(*cfg)
+        assert L.clbm_net_create(C.byref(c), 1, None, C.byref(h)) == clbm.CLBM_EINVAL
 
 
 def test_status_strings():
