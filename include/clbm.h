@@ -299,6 +299,21 @@ clbm_status clbm_net_train_step(clbm_net* net, const float* x, const float* targ
 clbm_status clbm_net_destroy(clbm_net* net);
 const char* clbm_net_last_error(const clbm_net* net);
 
+/* Replace the current state by the mean of the current and the previous
+ * post-collision states (both are kept by the ping-pong buffers), which
+ * cancels exactly any component that flips sign from one step to the next.
+ * The scheme on closed cavities has such a period-2 mode that does not
+ * decay: a rest start barely excites it, but an initialisation from
+ * predicted or interpolated fields can leave it at an amplitude that biases
+ * every instantaneous quantity (for instance a wall Nusselt number that
+ * alternates between two values).  Call after at least one step since the
+ * initialisation (else CLBM_EINVAL); enqueued on the context stream.  Not
+ * part of the paper's method. */
+clbm_status clbm_damp_period2(clbm_ctx* ctx);
+
+/* clbm_damp_period2 on every lattice of a batch (after a solve; synchronises). */
+clbm_status clbm_batch_damp_period2(clbm_batch* b);
+
 /* Number of time steps taken since the last initialisation. */
 clbm_status clbm_time(const clbm_ctx* ctx, int64_t* t_out);
 

@@ -50,6 +50,7 @@ class clbm_batch_item(C.Structure):
 EXPORTS = ["clbm_create", "clbm_set_boundaries", "clbm_init_fields", "clbm_step", "clbm_moments",
            "clbm_nusselt", "clbm_residual", "clbm_residual_fields_noalloc", "clbm_batch_create",
            "clbm_batch_solve", "clbm_batch_lattice", "clbm_batch_tile_width", "clbm_batch_destroy",
+           "clbm_damp_period2", "clbm_batch_damp_period2",
            "clbm_batch_last_error", "clbm_time", "clbm_destroy", "clbm_last_error",
            "clbm_status_string"]
 
@@ -96,6 +97,8 @@ def load(path: Optional[str] = None):
     L.clbm_batch_lattice.argtypes = [vp, C.c_int32, C.POINTER(vp)]
     L.clbm_batch_tile_width.argtypes = [vp, C.c_int32, C.POINTER(C.c_int32)]
     L.clbm_batch_destroy.argtypes = [vp]
+    L.clbm_damp_period2.argtypes = [vp]
+    L.clbm_batch_damp_period2.argtypes = [vp]
     L.clbm_batch_last_error.argtypes = [vp]
     L.clbm_batch_last_error.restype = C.c_char_p
     for name in EXPORTS:
@@ -205,6 +208,10 @@ def clbm_residual_fields_noalloc(T_now, ux_now, uy_now, T_prev, ux_prev, uy_prev
     _check(load().clbm_residual_fields_noalloc(*args, int(n), stream, C.byref(out)), None,
            "clbm_residual_fields_noalloc")
     return out.value
+
+
+def clbm_damp_period2(ctx):
+    _check(load().clbm_damp_period2(ctx), ctx, "clbm_damp_period2")
 
 
 def clbm_time(ctx) -> int:
@@ -374,6 +381,9 @@ class Batch:
 
     def solve(self, tol: float, max_steps: int, check_every: int = 100):
         return clbm_batch_solve(self.b, len(self), tol, max_steps, check_every)
+
+    def damp_period2(self):
+        _batch_check(load().clbm_batch_damp_period2(self.b), self.b, "clbm_batch_damp_period2")
 
     def view(self, i: int) -> C.c_void_p:
         return clbm_batch_lattice(self.b, i)

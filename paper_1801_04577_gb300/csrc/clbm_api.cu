@@ -492,6 +492,13 @@ clbm_status clbm_step(clbm_ctx* c, int64_t nsteps) {
   return CLBM_OK;
 }
 
+clbm_status clbm_damp_period2(clbm_ctx* c) {
+  if (!c) return CLBM_EINVAL;
+  if (c->t < 1) return fail(c, CLBM_EINVAL, "needs one step after initialisation");
+  CLBM_CUDA(c, c->L->average(c->buf[c->cur], c->buf[c->cur ^ 1], 14 * c->plane, c->stream));
+  return CLBM_OK;
+}
+
 clbm_status clbm_time(const clbm_ctx* c, int64_t* t_out) {
   if (!c || !t_out) return CLBM_EINVAL;
   *t_out = c->t;

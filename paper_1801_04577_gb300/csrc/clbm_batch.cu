@@ -414,6 +414,16 @@ clbm_status clbm_batch_create(const clbm_batch_item* items, int32_t n, int32_t a
   return CLBM_OK;
 }
 
+clbm_status clbm_batch_damp_period2(clbm_batch* b) {
+  if (!b) return CLBM_EINVAL;
+  for (int i = 0; i < b->n; ++i) {
+    clbm_status st = clbm_damp_period2(b->views[i]);
+    if (st != CLBM_OK) return bfail(b, st, "lattice " + std::to_string(i) + ": " + clbm_last_error(b->views[i]));
+  }
+  BCUDA(b, cudaStreamSynchronize(b->stream));
+  return CLBM_OK;
+}
+
 clbm_status clbm_batch_tile_width(const clbm_batch* b, int32_t i, int32_t* nodes_per_warp) {
   if (!b || !nodes_per_warp || i < 0 || i >= b->n) return CLBM_EINVAL;
   *nodes_per_warp = 32 * b->width[i];

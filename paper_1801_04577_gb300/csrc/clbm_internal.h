@@ -102,6 +102,8 @@ struct Launchers {
                                 cudaStream_t s);
   // persistent grid size (blocks) of the batched interior step for V
   int (*batch_grid)(int V);
+  // a <- (a + b) / 2 over n stored values
+  cudaError_t (*average)(void* a, const void* b, long long n, cudaStream_t s);
   // per-lattice residual: change of (T, ux, uy) since the previous check (snapshot), per step
   // (divided by K); 1e300 when there is no snapshot yet, +inf if a value is non-finite
   cudaError_t (*batch_residual)(const BatchLat* lats, const int* active, int* snap_valid,

@@ -892,6 +892,18 @@ __global__ void __launch_bounds__(kRedThreads)
   }
 }
 
+// a <- (a + b) / 2 over every stored value (both post-collision states of a
+// lattice, one step apart): cancels any component that flips sign each step.
+template <typename S>
+__global__ void average_state_kernel(S* __restrict__ a, const S* __restrict__ b, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    using R = typename Traits<S>::R;
+    const R v = R(0.5) * (to_r(a[i]) + to_r(b[i]));
+    a[i] = from_r<S, R>(v);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Launchers for one storage type
 // ---------------------------------------------------------------------------
@@ -1007,8 +1019,15 @@ struct LaunchImpl {
     return cudaGetLastError();
   }
 
+  static cudaError_t average(void* a, const void* b, long long n, cudaStream_t s) {
+    average_state_kernel<S><<<blocks_for(n, 256), 256, 0, s>>>(static_cast<S*>(a),
+                                                                 static_cast<const S*>(b), n);
+    return cudaGetLastError();
+  }
+
   static Launchers table() {
     Launchers L;
+    L.average = &average;
     L.batch_step = &batch_step;
     L.batch_boundary = &batch_boundary;
     L.batch_grid = &batch_grid;

@@ -415,3 +415,30 @@ def test_random_cavity_generator_properties():
         assert 0 < p.s_nu < 2 and 0 < p.lambda1 < 2
         if p.Q > 0:
             assert any(t[1] != 0 for t in w.geom.tbc)
+
+
+def test_scheme_has_neutral_period2_mode_on_closed_cavity():
+    """Characterisation of the scheme as specified (not a pin to an outside
+    value): restarting a steady 16^2 cavity from perturbed fields leaves a
+    step-to-step alternation of the wall Nusselt number that does not decay,
+    while the two-step mean returns to the steady value.  The CUDA library
+    offers clbm_damp_period2 for initialisations that excite it."""
+    w = I.natural_convection_cavity(16, 1e3)
+    o = oracle.from_workload(w)
+    o.step(20000)
+    rho, ux, uy, T = o.moments()
+    nu_ref = o.nusselt(0, 16, 1.0)
+    yy, xx = np.mgrid[0:16, 0:16]
+    f = I.Fields(ux=ux, uy=uy, T=T + 1e-2 * np.sin(np.pi * (xx + 0.5) / 16))
+    o2 = oracle.from_workload(I.Workload("restart", w.params, w.geom, f))
+    amps, means = [], []
+    for _ in range(3):
+        o2.step(3000)
+        a = o2.nusselt(0, 16, 1.0)
+        o2.step(1)
+        b = o2.nusselt(0, 16, 1.0)
+        amps.append(abs(a - b))
+        means.append(0.5 * (a + b))
+    assert amps[0] > 1e-6
+    assert amps[-1] > 0.9 * amps[0]           # neutral: no decay over 6000 steps
+    assert abs(means[-1] - nu_ref) < 1e-2 * amps[-1] + 1e-9
