@@ -308,9 +308,10 @@ def run_native(args):
                            parallelism=f"replicas{world}" if world > 1 else "single"),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
-                         "kernel": "clbm::step_kernel", "peak_kind": peak_kind,
+                         "kernel": "clbm::step_kernel + clbm::boundary_kernel (one step)",
+                         "peak_kind": peak_kind,
                          "algorithmic_bytes_per_launch": bytes_lu * nodes},
-            "gpu_launches": args.steps,
+            "gpu_launches": 2 * args.steps,  # interior + boundary kernel per step
             "residual_after": res}
     if e2e is not None:
         line["e2e"] = e2e

@@ -455,6 +455,18 @@ __device__ __forceinline__ void fixup(const DevGeom& g, const Co<R>& c, const S*
 // ---------------------------------------------------------------------------
 // The fused step kernel
 // ---------------------------------------------------------------------------
+// Store of one value (stochastically rounded for 16-bit storage when asked).
+template <typename S, typename R>
+__device__ __forceinline__ void st1(S* p, R v, int stochastic, uint32_t r) {
+  if constexpr (sizeof(S) == 2) {
+    if (stochastic) {
+      *reinterpret_cast<unsigned short*>(p) = (unsigned short)(cvt_rs2<S>(v, 0.0f, r) & 0xFFFFu);
+      return;
+    }
+  }
+  *p = from_r<S, R>(v);
+}
+
 // Interior update.  One warp updates the 32 * V nodes x = xw .. xw + 32V - 1
 // of row y (each lane owns V consecutive nodes); all 32 lanes must call it
 // together.  Every node is pulled and collided as if it were an interior
@@ -463,7 +475,7 @@ __device__ __forceinline__ void fixup(const DevGeom& g, const Co<R>& c, const S*
 // next to solids come out wrong here and are recomputed afterwards by the
 // boundary kernel from its precomputed node list.  Keeping the walls out of
 // this kernel keeps its warps free of divergent wall code.
-template <typename S, int V>
+template <typename S, int V, bool SKIP_EDGES = false>
 __device__ __forceinline__ void step_tile(const DevGeom& g, const Co<typename Traits<S>::R>& c,
                                           const S* __restrict__ src, S* __restrict__ dst, int y,
                                           int xw, int lane, uint32_t seed, int stochastic) {
@@ -524,6 +536,22 @@ __device__ __forceinline__ void step_tile(const DevGeom& g, const Co<typename Tr
   }
 
   S* out = dst + (long long)y * g.pitch + x0;
+  if constexpr (SKIP_EDGES) {
+    // leave the first and last column to the boundary update running alongside
+    if (x0 == 0 || (x0 <= g.nx - 1 && g.nx - 1 < x0 + V)) {
+      const uint32_t key = seed ^ mix32((uint32_t)((long long)y * g.pitch + x0));
+#pragma unroll
+      for (int k = 0; k < V; ++k) {
+        const int x = x0 + k;
+        if (x == 0 || x == g.nx - 1) continue;
+#pragma unroll
+        for (int q = 0; q < 14; ++q)
+          st1<S, R>(out + q * plane + k, v[q][k], stochastic,
+                    mix32(key + 0x9E3779B9u * (uint32_t)(q + 1) + 0x632BE5ABu * (uint32_t)k));
+      }
+      return;
+    }
+  }
   if constexpr (sizeof(S) == 2) {
     if (stochastic) {
       const uint32_t key = seed ^ mix32((uint32_t)((long long)y * g.pitch + x0));
@@ -538,18 +566,6 @@ __device__ __forceinline__ void step_tile(const DevGeom& g, const Co<typename Tr
   }
 #pragma unroll
   for (int q = 0; q < 14; ++q) stv<S, V>(out + q * plane, v[q]);
-}
-
-// Store of one value (stochastically rounded for 16-bit storage when asked).
-template <typename S, typename R>
-__device__ __forceinline__ void st1(S* p, R v, int stochastic, uint32_t r) {
-  if constexpr (sizeof(S) == 2) {
-    if (stochastic) {
-      *reinterpret_cast<unsigned short*>(p) = (unsigned short)(cvt_rs2<S>(v, 0.0f, r) & 0xFFFFu);
-      return;
-    }
-  }
-  *p = from_r<S, R>(v);
 }
 
 // Boundary update of node index i (pitch layout): pull with clamped indices,
@@ -607,6 +623,35 @@ __global__ void __launch_bounds__(kRedThreads) boundary_kernel(const StepArgs a)
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < a.nb; k += gridDim.x * blockDim.x)
     step_node<S, MASK>(a.g, c, static_cast<const S*>(a.src), static_cast<S*>(a.dst), a.bnodes[k],
                        a.seed, a.stochastic);
+}
+
+// Box lattices (no mask): interior and boundary nodes are disjoint, so one
+// launch does both.  The first nbb blocks update the boundary list (first and
+// last column, first and last row of a non-periodic y axis); the others are
+// interior tiles of rows that are not boundary rows, which skip the first and
+// last column.  The latency-bound boundary work then overlaps the streaming
+// interior work instead of following it.
+template <typename S>
+__global__ void __launch_bounds__(kStepThreads, 5) step_fused_kernel(const StepArgs a, int nbb,
+                                                                  int xblocks, int y0) {
+  using R = typename Traits<S>::R;
+  constexpr int V = Traits<S>::V;
+  const Co<R> c = make_co<R>(a.c);
+  if ((int)blockIdx.x < nbb) {
+    const int k = blockIdx.x * kStepThreads + threadIdx.x;
+    if (k < a.nb)
+      step_node<S, false>(a.g, c, static_cast<const S*>(a.src), static_cast<S*>(a.dst), a.bnodes[k],
+                          a.seed, a.stochastic);
+    return;
+  }
+  const int b = blockIdx.x - nbb;
+  const int y = y0 + b / xblocks;
+  const int lane = threadIdx.x & 31;
+  const int warp = (b % xblocks) * (kStepThreads / 32) + (threadIdx.x >> 5);
+  const int xw = warp * 32 * V;
+  if (xw >= a.g.nx) return;  // whole warps only
+  step_tile<S, V, true>(a.g, c, static_cast<const S*>(a.src), static_cast<S*>(a.dst), y, xw, lane,
+                        a.seed, a.stochastic);
 }
 
 // ---------------------------------------------------------------------------
@@ -913,7 +958,18 @@ struct LaunchImpl {
 
   static cudaError_t step(const StepArgs& a, cudaStream_t s) {
     const int nodes_per_block = kStepThreads * V;
-    dim3 grid((a.g.nx + nodes_per_block - 1) / nodes_per_block, a.g.ny);
+    const int xblocks = (a.g.nx + nodes_per_block - 1) / nodes_per_block;
+    if (!a.g.flags) {  // box lattice: one fused launch
+      const int y0 = a.g.py ? 0 : 1;
+      const int rows = a.g.py ? a.g.ny : (a.g.ny > 2 ? a.g.ny - 2 : 0);
+      const int nbb = (a.nb + kStepThreads - 1) / kStepThreads;
+      const long long blocks = (long long)nbb + (long long)xblocks * rows;
+      if (blocks > 0 && blocks < (1LL << 31)) {
+        step_fused_kernel<S><<<(unsigned)blocks, kStepThreads, 0, s>>>(a, nbb, xblocks, y0);
+        return cudaGetLastError();
+      }
+    }
+    dim3 grid(xblocks, a.g.ny);
     step_kernel<S><<<grid, kStepThreads, 0, s>>>(a);
     if (a.nb > 0) {
       const int blocks = (a.nb + kRedThreads - 1) / kRedThreads;
