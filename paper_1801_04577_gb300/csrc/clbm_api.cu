@@ -61,8 +61,21 @@ struct clbm_ctx {
   double* d_fields = nullptr;  // 4 * nx * ny doubles, allocated on first use
   double* d_part = nullptr;    // reduction partials + result
   std::map<int, std::pair<NuLink*, int>> nu_lists;
+  // captured graphs of kGraphSteps steps, keyed by (current buffer, step parity)
+  long long* d_t = nullptr;
+  cudaGraphExec_t step_graph[4] = {nullptr, nullptr, nullptr, nullptr};
   std::string err;
 };
+
+constexpr int kGraphSteps = 32;
+
+static void drop_graphs(clbm_ctx* c) {
+  for (auto& g : c->step_graph)
+    if (g) {
+      cudaGraphExecDestroy(g);
+      g = nullptr;
+    }
+}
 
 static clbm_status fail(clbm_ctx* c, clbm_status s, const std::string& msg) {
   if (c) c->err = msg;
@@ -193,6 +206,8 @@ const char* clbm_last_error(const clbm_ctx* ctx) { return ctx ? ctx->err.c_str()
 clbm_status clbm_destroy(clbm_ctx* c) {
   if (!c) return CLBM_OK;
   if (c->stream) cudaStreamSynchronize(c->stream);
+  drop_graphs(c);
+  cudaFree(c->d_t);
   free_tables(c);
   if (!c->borrowed) {
     cudaFree(c->buf[0]);
@@ -390,6 +405,7 @@ clbm_status clbm_set_boundaries(clbm_ctx* c, const uint8_t* solid, const clbm_tb
     }
     // upload
     CLBM_CUDA(c, cudaStreamSynchronize(c->stream));
+    drop_graphs(c);  // captured steps hold the old wall description
     free_tables(c);
     if (masked) {
       const size_t np = (size_t)ny * c->pitch;
@@ -471,19 +487,70 @@ clbm_status clbm_init_fields(clbm_ctx* c, const double* rho, const double* ux, c
   return CLBM_OK;
 }
 
-clbm_status clbm_step(clbm_ctx* c, int64_t nsteps) {
-  if (!c || nsteps < 0) return fail(c, CLBM_EINVAL, "bad step count");
-  if (!c->have_walls) return fail(c, CLBM_EINVAL, "non-periodic lattice: call clbm_set_boundaries first");
+static StepArgs step_args(const clbm_ctx* c, int cur, int64_t t) {
   StepArgs a;
   a.g = make_geom(c);
   a.c = make_coef(c);
   a.stochastic = c->p.rounding;
   a.bnodes = c->d_bnodes;
   a.nb = (int)c->h_bnodes.size();
+  a.src = c->buf[cur];
+  a.dst = c->buf[cur ^ 1];
+  a.seed = (uint32_t)(t * 0x9E3779B1ull) ^ (uint32_t)(t >> 32);
+  a.reverse = (int)(t & 1);
+  a.tdev = nullptr;
+  a.tstep = 0;
+  return a;
+}
+
+// Capture kGraphSteps steps starting from buffer `cur` at a step of parity `par`.
+static clbm_status capture_steps(clbm_ctx* c, int cur, int par, cudaGraphExec_t* out) {
+  if (!c->d_t) CLBM_CUDA(c, cudaMalloc(&c->d_t, sizeof(long long)));
+  cudaGraph_t graph;
+  CLBM_CUDA(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+  cudaError_t e = cudaSuccess;
+  for (int j = 0; j < kGraphSteps && e == cudaSuccess; ++j) {
+    StepArgs a = step_args(c, (cur + j) & 1, par + j);
+    a.tdev = c->d_t;
+    a.tstep = j;
+    e = c->L->step(a, c->stream);
+  }
+  if (e == cudaSuccess) e = launch_advance(c->d_t, kGraphSteps, c->stream);
+  cudaError_t e2 = cudaStreamEndCapture(c->stream, &graph);
+  if (e != cudaSuccess || e2 != cudaSuccess) {
+    if (e2 == cudaSuccess) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    return cuda_fail(c, e != cudaSuccess ? e : e2, "capture of the step graph");
+  }
+  e = cudaGraphInstantiate(out, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return cuda_fail(c, e, "instantiate the step graph");
+  return CLBM_OK;
+}
+
+clbm_status clbm_step(clbm_ctx* c, int64_t nsteps) {
+  if (!c || nsteps < 0) return fail(c, CLBM_EINVAL, "bad step count");
+  if (!c->have_walls) return fail(c, CLBM_EINVAL, "non-periodic lattice: call clbm_set_boundaries first");
+  // Long runs replay a captured graph of kGraphSteps launches (fewer launch
+  // gaps); the step count then lives on the device.  Not while the caller is
+  // capturing the stream itself.
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  CLBM_CUDA(c, cudaStreamIsCapturing(c->stream, &cs));
+  if (nsteps >= kGraphSteps && cs == cudaStreamCaptureStatusNone) {
+    const int key = c->cur * 2 + (int)(c->t & 1);
+    if (!c->step_graph[key]) {
+      clbm_status st = capture_steps(c, c->cur, (int)(c->t & 1), &c->step_graph[key]);
+      if (st != CLBM_OK) return st;
+    }
+    CLBM_CUDA(c, launch_set_step(c->d_t, c->t, c->stream));
+    while (nsteps >= kGraphSteps) {
+      CLBM_CUDA(c, cudaGraphLaunch(c->step_graph[key], c->stream));
+      c->t += kGraphSteps;  // kGraphSteps is even: the current buffer is unchanged
+      nsteps -= kGraphSteps;
+    }
+  }
   for (int64_t s = 0; s < nsteps; ++s) {
-    a.src = c->buf[c->cur];
-    a.dst = c->buf[c->cur ^ 1];
-    a.seed = (uint32_t)(c->t * 0x9E3779B1ull) ^ (uint32_t)(c->t >> 32);
+    StepArgs a = step_args(c, c->cur, c->t);
     cudaError_t e = c->L->step(a, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "step kernel launch");
     c->cur ^= 1;

@@ -47,6 +47,9 @@ struct StepArgs {
   int stochastic;   // 16-bit stores: 0 = nearest even, 1 = stochastic
   const int32_t* bnodes;  // boundary nodes (pitch-layout indices) recomputed after the interior
   int nb;
+  int reverse;  // walk the rows from the last one (alternate steps: reuse of L2-resident rows)
+  const long long* tdev;  // if set: the step count lives on the device (graph replays); seed from *tdev + tstep
+  int tstep;
 };
 
 // One Nusselt link, prepared on the host: node index (pitch layout) of x_f,
@@ -104,6 +107,7 @@ struct Launchers {
   int (*batch_grid)(int V);
   // a <- (a + b) / 2 over n stored values
   cudaError_t (*average)(void* a, const void* b, long long n, cudaStream_t s);
+
   // per-lattice residual: change of (T, ux, uy) since the previous check (snapshot), per step
   // (divided by K); 1e300 when there is no snapshot yet, +inf if a value is non-finite
   cudaError_t (*batch_residual)(const BatchLat* lats, const int* active, int* snap_valid,
@@ -132,6 +136,10 @@ clbm_status create_view(const clbm_params* p, cudaStream_t s, void* buf_a, void*
                         clbm_ctx** out);
 ViewInfo describe_view(const clbm_ctx* c);
 void set_view_time(clbm_ctx* c, int64_t t, int cur);
+
+// *t += k on the device (advances the step counter of a captured step graph)
+cudaError_t launch_advance(long long* t, int k, cudaStream_t s);
+cudaError_t launch_set_step(long long* t, long long v, cudaStream_t s);
 
 // Fixed-order sum of nblocks x width partials into out[width] (one block).
 cudaError_t launch_reduce_partials(const double* partials, int nblocks, int width, double* out,

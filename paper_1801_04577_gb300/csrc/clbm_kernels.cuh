@@ -601,6 +601,15 @@ __device__ __forceinline__ void step_node(const DevGeom& g, const Co<typename Tr
   }
 }
 
+// Stochastic-rounding key of a step: from the host value, or from the device
+// step counter when the launch is part of a replayed graph.
+__device__ __forceinline__ uint32_t step_seed(const StepArgs& a) {
+  if (!a.stochastic) return 0u;
+  if (!a.tdev) return a.seed;
+  const long long t = *a.tdev + a.tstep;
+  return (uint32_t)(t * 0x9E3779B1ull) ^ (uint32_t)(t >> 32);
+}
+
 // One launch = the interior update of one time step of one lattice.
 template <typename S>
 __global__ void __launch_bounds__(kStepThreads) step_kernel(const StepArgs a) {
@@ -611,8 +620,9 @@ __global__ void __launch_bounds__(kStepThreads) step_kernel(const StepArgs a) {
   const int xw = warp * 32 * V;
   if (xw >= a.g.nx) return;  // whole warps only: the shuffles need all 32 lanes
   const Co<R> c = make_co<R>(a.c);
-  step_tile<S, V>(a.g, c, static_cast<const S*>(a.src), static_cast<S*>(a.dst), blockIdx.y, xw,
-                  lane, a.seed, a.stochastic);
+  const int y = a.reverse ? a.g.ny - 1 - (int)blockIdx.y : (int)blockIdx.y;
+  step_tile<S, V>(a.g, c, static_cast<const S*>(a.src), static_cast<S*>(a.dst), y, xw, lane,
+                  step_seed(a), a.stochastic);
 }
 
 // The boundary nodes of the same step (launched after step_kernel).
@@ -620,9 +630,10 @@ template <typename S, bool MASK>
 __global__ void __launch_bounds__(kRedThreads) boundary_kernel(const StepArgs a) {
   using R = typename Traits<S>::R;
   const Co<R> c = make_co<R>(a.c);
+  const uint32_t seed = step_seed(a);
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < a.nb; k += gridDim.x * blockDim.x)
     step_node<S, MASK>(a.g, c, static_cast<const S*>(a.src), static_cast<S*>(a.dst), a.bnodes[k],
-                       a.seed, a.stochastic);
+                       seed, a.stochastic);
 }
 
 // Box lattices (no mask): interior and boundary nodes are disjoint, so one
@@ -641,17 +652,19 @@ __global__ void __launch_bounds__(kStepThreads, 5) step_fused_kernel(const StepA
     const int k = blockIdx.x * kStepThreads + threadIdx.x;
     if (k < a.nb)
       step_node<S, false>(a.g, c, static_cast<const S*>(a.src), static_cast<S*>(a.dst), a.bnodes[k],
-                          a.seed, a.stochastic);
+                          step_seed(a), a.stochastic);
     return;
   }
   const int b = blockIdx.x - nbb;
-  const int y = y0 + b / xblocks;
+  const int rows = a.g.py ? a.g.ny : a.g.ny - 2;
+  const int row = b / xblocks;
+  const int y = y0 + (a.reverse ? rows - 1 - row : row);
   const int lane = threadIdx.x & 31;
   const int warp = (b % xblocks) * (kStepThreads / 32) + (threadIdx.x >> 5);
   const int xw = warp * 32 * V;
   if (xw >= a.g.nx) return;  // whole warps only
   step_tile<S, V, true>(a.g, c, static_cast<const S*>(a.src), static_cast<S*>(a.dst), y, xw, lane,
-                        a.seed, a.stochastic);
+                        step_seed(a), a.stochastic);
 }
 
 // ---------------------------------------------------------------------------

@@ -21,6 +21,19 @@ __global__ void __launch_bounds__(kRedThreads)
   }
 }
 
+__global__ void advance_kernel(long long* t, int k) { *t += k; }
+__global__ void set_kernel(long long* t, long long v) { *t = v; }
+
+cudaError_t launch_set_step(long long* t, long long v, cudaStream_t s) {
+  set_kernel<<<1, 1, 0, s>>>(t, v);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_advance(long long* t, int k, cudaStream_t s) {
+  advance_kernel<<<1, 1, 0, s>>>(t, k);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_reduce_partials(const double* partials, int nblocks, int width, double* out,
                                    cudaStream_t s) {
   reduce_partials_kernel<<<1, kRedThreads, 0, s>>>(partials, nblocks, width, out);
