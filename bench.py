@@ -213,6 +213,20 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
+def combine_ranks(elapsed_ms: float, nodes: int, steps: int, device=None):
+    """Whole-job throughput of independent replicas: the slowest rank's time
+    (max over ranks) bounds the job; every rank advanced `nodes` nodes for
+    `steps` steps.  Returns (max elapsed ms, MLUPS over all ranks)."""
+    import torch
+    import torch.distributed as dist
+    world = dist.get_world_size() if dist.is_available() and dist.is_initialized() else 1
+    t = torch.tensor([elapsed_ms], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    el = float(t.item())
+    return el, world * nodes * steps / (el * 1e-3) / 1e6
+
+
 def run_native(args):
     import torch
     import torch.distributed as dist
@@ -261,11 +275,7 @@ def run_native(args):
     # the state must still be finite after the timed steps
     res = s.residual()
 
-    el_t = torch.tensor([el_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(el_t, op=dist.ReduceOp.MAX)
-    el_ms = float(el_t.item())
-    value = world * nodes * args.steps / (el_ms * 1e-3) / 1e6
+    el_ms, value = combine_ranks(el_ms, nodes, args.steps, dev)
 
     # end to end through the public API: host fields in, solve, host fields out
     e2e = None

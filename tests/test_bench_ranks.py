@@ -1,0 +1,50 @@
+"""Host logic of the multi-process benchmark path on CPU: two gloo ranks run
+independent replicas; the job time is the slowest rank's and the throughput
+counts every rank's nodes (weak scaling)."""
+import os
+import socket
+
+import pytest
+
+torch = pytest.importorskip("torch")
+import torch.distributed as dist  # noqa: E402
+import torch.multiprocessing as mp  # noqa: E402
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank, world, port, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+    el, mlups = bench.combine_ranks(10.0 * (rank + 1), nodes=1000, steps=50)
+    q.put((rank, el, mlups))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_rank_timing_is_max_over_ranks():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    out = [q.get(timeout=120) for _ in procs]
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for rank, el, mlups in out:
+        assert el == pytest.approx(20.0)                      # slowest rank
+        assert mlups == pytest.approx(2 * 1000 * 50 / 20e-3 / 1e6)
+
+
+def test_single_process_has_no_collective():
+    import bench
+    el, mlups = bench.combine_ranks(5.0, nodes=100, steps=10)
+    assert el == 5.0 and mlups == pytest.approx(100 * 10 / 5e-3 / 1e6)
