@@ -33,7 +33,8 @@ class OrefParams(C.Structure):
                 ("s_4", C.c_double), ("lambda0", C.c_double), ("lambda1", C.c_double),
                 ("lambda2", C.c_double), ("rho0", C.c_double), ("T0", C.c_double),
                 ("gbeta", C.c_double), ("Fvx", C.c_double), ("Fvy", C.c_double),
-                ("Q", C.c_double), ("cT2", C.c_double)]
+                ("Q", C.c_double), ("cT2", C.c_double), ("viscous_heating", C.c_int32),
+                ("reserved1", C.c_int32)]
 
 
 def build(force: bool = False) -> str:
@@ -114,7 +115,7 @@ def _f64(a, shape=None):
 def make_params(p) -> OrefParams:
     return OrefParams(p.nx, p.ny, p.periodic_x, p.periodic_y, p.s_nu, p.s_b, p.s_3, p.s_4,
                       p.lambda0, p.lambda1, p.lambda2, p.rho0, p.T0, p.gbeta, p.Fvx, p.Fvy,
-                      p.Q, p.cT2)
+                      p.Q, p.cT2, int(getattr(p, "viscous_heating", 0)), 0)
 
 
 class Oracle:

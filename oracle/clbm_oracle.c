@@ -59,6 +59,7 @@ typedef struct {
   int32_t nx, ny, periodic_x, periodic_y;
   double s_nu, s_b, s_3, s_4, lambda0, lambda1, lambda2;
   double rho0, T0, gbeta, Fvx, Fvy, Q, cT2;
+  int32_t viscous_heating, reserved1; /* 1: add the viscous dissipation source (Sec. 3.2) */
 } oref_params;
 
 /* ---------------- small dense linear algebra ---------------- */
@@ -175,6 +176,7 @@ typedef struct {
   int32_t ntbc;
   double *f, *g, *fn, *gn;     /* pre-collision DFs at t, and at t+1        */
   double *T, *rho, *ux, *uy;   /* macroscopic fields at time t (of the last step) */
+  double* Qn;                  /* total heat source per node at time t          */
   int have_prev;
   int64_t steps;
 } oref_ctx;
@@ -213,9 +215,29 @@ static int is_fluid(const oref_ctx* c, int x, int y) {
 
 /* ---------------- node-level building blocks ---------------- */
 
-/* Macroscopic fields of one node from its pre-collision DFs (Eq. 25, 2, 12). */
+/* Viscous dissipation source of Sec. 3.2, Q_v = nu (du/dy)^2 for the channel;
+ * in general nu (D^2 + G^2) with D = dux/dx - duy/dy, G = duy/dx + dux/dy (the
+ * dissipation 2 nu S:S of a divergence-free flow).  The strain rate is read
+ * from the pre-collision non-equilibrium central moments: the stress
+ * (1 - s/2) k~^neq equals rho nu times the strain with nu = (1/s_nu - 1/2)/3,
+ * so G = -3 s_nu k~11 / rho and D = -3 s_nu (k~20 - k~02) / (2 rho). */
+static double viscous_source(const oref_ctx* c, const double* f, double rho, double ux, double uy) {
+  double N[81], k[9], kt[9];
+  matvec(9, M9, f, k);
+  shift9(ux, uy, N);
+  matvec(9, N, k, kt); /* order of Eq. 5: kt[3] = k~20, kt[4] = k~02, kt[5] = k~11 */
+  const double nu = (1.0 / c->p.s_nu - 0.5) / 3.0;
+  const double G = -3.0 * c->p.s_nu * kt[5] / rho;
+  const double D = -1.5 * c->p.s_nu * (kt[3] - kt[4]) / rho;
+  return nu * (D * D + G * G);
+}
+
+/* Macroscopic fields of one node from its pre-collision DFs (Eq. 25, 2, 12);
+ * *Q receives the total heat source at the node.  With viscous heating the
+ * Boussinesq force uses T without the viscous source's half (the source needs
+ * u, which needs the force). */
 static void macros(const oref_ctx* c, const double* f, const double* g, double* rho, double* ux,
-                   double* uy, double* T, double* Fx, double* Fy) {
+                   double* uy, double* T, double* Fx, double* Fy, double* Q) {
   double t = 0.0;
   for (int i = 0; i < 5; ++i) t += g[i];
   t += 0.5 * c->p.Q; /* Eq. 25 */
@@ -230,9 +252,16 @@ static void macros(const oref_ctx* c, const double* f, const double* g, double* 
   *rho = r;
   *ux = (jx + 0.5 * fx) / r; /* Eq. 12 */
   *uy = (jy + 0.5 * fy) / r;
+  double q = c->p.Q;
+  if (c->p.viscous_heating) {
+    const double qv = viscous_source(c, f, r, *ux, *uy);
+    q += qv;
+    t += 0.5 * qv; /* Eq. 25 with the total source */
+  }
   *T = t;
   *Fx = fx;
   *Fy = fy;
+  if (Q) *Q = q;
 }
 
 /* Flow collision (Eq. 6-10) and back-transformation (text after Eq. 11). */
@@ -267,11 +296,11 @@ static void collide_flow(const oref_ctx* c, const double* f, double rho, double 
   matvec(9, c->Minv, raw, fs);
 }
 
-/* Thermal collision with source (Eq. 15, 19, 23, 24) and Eq. 20. */
+/* Thermal collision with source Q (Eq. 15, 19, 23, 24) and Eq. 20. */
 static void collide_thermal(const oref_ctx* c, const double* g, double ux, double uy, double T,
-                            double* gs) {
+                            double Q, double* gs) {
   double N[25], k[5], kt[5], a[5], b[5], r5[5], ks[5], raw[5];
-  const double cT2 = c->p.cT2, Q = c->p.Q;
+  const double cT2 = c->p.cT2;
   matvec(5, M5, g, k);
   shift5(ux, uy, N);
   matvec(5, N, k, kt);
@@ -355,6 +384,7 @@ void oref_destroy(void* h) {
   free(c->rho);
   free(c->ux);
   free(c->uy);
+  free(c->Qn);
   free(c);
 }
 
@@ -383,11 +413,12 @@ int oref_create(const oref_params* p, const uint8_t* solid, const double* tbc, i
   c->rho = (double*)calloc(n, sizeof(double));
   c->ux = (double*)calloc(n, sizeof(double));
   c->uy = (double*)calloc(n, sizeof(double));
+  c->Qn = (double*)calloc(n, sizeof(double));
   c->solid = (uint8_t*)calloc(n, 1);
   c->wtbc = (int32_t*)malloc(5 * n * sizeof(int32_t));
   c->wne = (double*)calloc(5 * n, sizeof(double));
   c->tbc = (double*)calloc(3 * (ntbc > 0 ? ntbc : 1), sizeof(double));
-  if (!c->f || !c->g || !c->fn || !c->gn || !c->T || !c->rho || !c->ux || !c->uy || !c->solid ||
+  if (!c->f || !c->g || !c->fn || !c->gn || !c->T || !c->rho || !c->ux || !c->uy || !c->Qn || !c->solid ||
       !c->wtbc || !c->wne || !c->tbc) {
     oref_destroy(c);
     return OREF_ENOMEM;
@@ -486,10 +517,11 @@ static void step_once(oref_ctx* c) {
       int64_t k = idx(c, x, y);
       double Fx, Fy;
       if (!is_fluid(c, x, y)) {
-        c->rho[k] = c->ux[k] = c->uy[k] = c->T[k] = 0.0;
+        c->rho[k] = c->ux[k] = c->uy[k] = c->T[k] = c->Qn[k] = 0.0;
         continue;
       }
-      macros(c, c->f + 9 * k, c->g + 5 * k, &c->rho[k], &c->ux[k], &c->uy[k], &c->T[k], &Fx, &Fy);
+      macros(c, c->f + 9 * k, c->g + 5 * k, &c->rho[k], &c->ux[k], &c->uy[k], &c->T[k], &Fx, &Fy,
+             &c->Qn[k]);
     }
   /* collide, stream (Eq. 11, 21) and apply the wall rules */
 #pragma omp parallel for schedule(static) if (c->n >= 2048)
@@ -503,9 +535,11 @@ static void step_once(oref_ctx* c) {
       }
       double fs[9], gs[5];
       const double Fx = c->p.Fvx;
-      const double Fy = c->p.Fvy + c->p.rho0 * c->p.gbeta * (c->T[k] - c->p.T0);
+      /* force temperature: T without the viscous source's half (see macros) */
+      const double Tf = c->T[k] - 0.5 * (c->Qn[k] - c->p.Q);
+      const double Fy = c->p.Fvy + c->p.rho0 * c->p.gbeta * (Tf - c->p.T0);
       collide_flow(c, c->f + 9 * k, c->rho[k], c->ux[k], c->uy[k], Fx, Fy, fs);
-      collide_thermal(c, c->g + 5 * k, c->ux[k], c->uy[k], c->T[k], gs);
+      collide_thermal(c, c->g + 5 * k, c->ux[k], c->uy[k], c->T[k], c->Qn[k], gs);
       for (int i = 0; i < 9; ++i) {
         int xo, yo, side;
         if (neighbour(c, x, y, EX[i], EY[i], &xo, &yo, &side) && is_fluid(c, xo, yo)) {
@@ -551,7 +585,7 @@ int oref_moments(void* h, double* rho, double* ux, double* uy, double* T) {
   oref_ctx* c = (oref_ctx*)h;
   for (int64_t k = 0; k < c->n; ++k) {
     double r = 0, u = 0, v = 0, t = 0, Fx, Fy;
-    if (!c->solid[k]) macros(c, c->f + 9 * k, c->g + 5 * k, &r, &u, &v, &t, &Fx, &Fy);
+    if (!c->solid[k]) macros(c, c->f + 9 * k, c->g + 5 * k, &r, &u, &v, &t, &Fx, &Fy, NULL);
     if (rho) rho[k] = r;
     if (ux) ux[k] = u;
     if (uy) uy[k] = v;
@@ -623,7 +657,7 @@ int oref_residual(void* h, double* r) {
   for (int64_t k = 0; k < c->n; ++k) {
     if (c->solid[k]) continue;
     double rr, u, v, t, Fx, Fy;
-    macros(c, c->f + 9 * k, c->g + 5 * k, &rr, &u, &v, &t, &Fx, &Fy);
+    macros(c, c->f + 9 * k, c->g + 5 * k, &rr, &u, &v, &t, &Fx, &Fy, NULL);
     const double now[3] = {t, u, v}, prev[3] = {c->T[k], c->ux[k], c->uy[k]};
     for (int q = 0; q < 3; ++q) {
       d[q] += (now[q] - prev[q]) * (now[q] - prev[q]);
@@ -681,10 +715,10 @@ void oref_thermal_from_central(void* h, const double* kt, double ux, double uy, 
 void oref_collide_node(void* h, const double* f, const double* g, double* fs, double* gs,
                        double* mac) {
   oref_ctx* c = (oref_ctx*)h;
-  double rho, ux, uy, T, Fx, Fy;
-  macros(c, f, g, &rho, &ux, &uy, &T, &Fx, &Fy);
+  double rho, ux, uy, T, Fx, Fy, Q;
+  macros(c, f, g, &rho, &ux, &uy, &T, &Fx, &Fy, &Q);
   collide_flow(c, f, rho, ux, uy, Fx, Fy, fs);
-  collide_thermal(c, g, ux, uy, T, gs);
+  collide_thermal(c, g, ux, uy, T, Q, gs);
   mac[0] = rho;
   mac[1] = ux;
   mac[2] = uy;

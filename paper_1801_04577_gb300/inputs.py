@@ -66,6 +66,7 @@ class Params:
     Fvy: float = 0.0
     Q: float = 0.0
     cT2: float = CT2_PAPER
+    viscous_heating: int = 0  # 1: add the viscous dissipation source of Sec. 3.2
 
 
 @dataclasses.dataclass
@@ -349,6 +350,26 @@ def poiseuille_channel(ny: int = 8, nu: float = 0.1, Fx: float = 1e-5, nx: int =
     g = Geometry(tbc=[dirichlet(Tw)], side_tbc=(-1, -1, 0, 0))
     return Workload(f"poiseuille_{ny}", p, g, Fields(T=np.full((ny, nx), Tw)), length=float(ny),
                     u_scale=Fx * ny * ny / (8.0 * nu))
+
+
+def dissipation_channel(L: int = 16, nu: float = 0.1, alpha: float = 0.1, Fx: float = 1e-5,
+                        nx: int = 4, Tw: float = 0.0) -> Workload:
+    """Poiseuille flow with viscous heating (Sec. 3.2): body force Fx between
+    no-slip walls at y = 0 and y = L held at Tw, heat source nu (du/dy)^2."""
+    s_nu, lambda1 = rates_from_diffusivities(nu, alpha)
+    p = Params(nx=nx, ny=L, periodic_x=1, s_nu=s_nu, s_b=s_nu, lambda1=lambda1, Fvx=Fx, T0=Tw,
+               viscous_heating=1)
+    g = Geometry(tbc=[dirichlet(Tw)], side_tbc=(-1, -1, 0, 0))
+    return Workload(f"dissipation_{L}", p, g, Fields(T=np.full((L, nx), Tw)), length=float(L),
+                    u_scale=Fx * L * L / (8.0 * nu))
+
+
+def dissipation_exact(L: int, nu: float, alpha: float, Fx: float, Tw: float = 0.0) -> np.ndarray:
+    """Exact profile of Sec. 3.2 at the node centres: Tw + (h^2 Fx / 2)^2 [1 - (y/h)^4] / (3 nu alpha),
+    y measured from the channel centre, h the half-width."""
+    h = L / 2.0
+    y = np.arange(L) + 0.5 - h
+    return Tw + (h * h * Fx / 2.0) ** 2 * (1.0 - (y / h) ** 4) / (3.0 * nu * alpha)
 
 
 def poiseuille_exact(ny: int, nu: float, Fx: float, rho0: float = 1.0) -> np.ndarray:

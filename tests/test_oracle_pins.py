@@ -442,3 +442,23 @@ def test_scheme_has_neutral_period2_mode_on_closed_cavity():
     assert amps[0] > 1e-6
     assert amps[-1] > 0.9 * amps[0]           # neutral: no decay over 6000 steps
     assert abs(means[-1] - nu_ref) < 1e-2 * amps[-1] + 1e-9
+
+
+def test_viscous_dissipation_poiseuille_profile_and_order(paper_values):
+    """Sec. 3.2: Poiseuille flow with the viscous heat source reproduces the
+    exact quartic temperature profile, with second-order convergence (the
+    paper reports a slope of 2.05 for E2 against the grid size)."""
+    nu, alpha = 0.1, 0.1
+    errs = []
+    Ls = (8, 16, 32)
+    for L in Ls:
+        Fx = 1e-5 * (16.0 / L) ** 2
+        w = I.dissipation_channel(L, nu, alpha, Fx, nx=1)
+        o = oracle.from_workload(w)
+        o.step(int(20 * L * L / alpha) + 2000)
+        T = o.moments()[3][:, 0]
+        Ta = I.dissipation_exact(L, nu, alpha, Fx)
+        errs.append(_E2(T, Ta))
+    assert errs[1] < 1e-2
+    slope = -np.polyfit(np.log(Ls), np.log(errs), 1)[0]
+    assert abs(slope - paper_values["poiseuille_dissipation_slope"]["slope"]) < 0.15
