@@ -76,7 +76,13 @@ typedef enum {
  *   gbeta : g * beta; the buoyancy force density is rho0 gbeta (T - T0) along +y (Eq. 2)
  *   Fvx, Fvy : external body force density F_v (Eq. 2)
  *   Q     : uniform volumetric heat source (Eq. 23-25)
- *   cT2   : squared D2Q5 sound speed c_T^2 (Eq. 19; 2/5 in Sec. 3) */
+ *   cT2   : squared D2Q5 sound speed c_T^2 (Eq. 19; 2/5 in Sec. 3)
+ *   viscous_heating : 1 adds the viscous dissipation source of Sec. 3.2 to Q at
+ *           every node, Q_v = nu (D^2 + G^2) with D = dux/dx - duy/dy and
+ *           G = duy/dx + dux/dy (= nu (du/dy)^2 in a channel), the strain read
+ *           from the node's pre-collision non-equilibrium central moments
+ *           (G = -3 s_nu k~11/rho, D = -3 s_nu (k~20 - k~02)/(2 rho)); the
+ *           Boussinesq force then uses T without Q_v/2.  Adds one stored plane. */
 typedef struct {
   int32_t nx, ny;
   int32_t periodic_x, periodic_y;
@@ -85,6 +91,8 @@ typedef struct {
   double s_nu, s_b, s_3, s_4;
   double lambda0, lambda1, lambda2;
   double rho0, T0, gbeta, Fvx, Fvy, Q, cT2;
+  int32_t viscous_heating;
+  int32_t reserved1;
 } clbm_params;
 
 /* Thermal wall condition b1 dT/dn + b2 T = b3 (Sec. 2.3), n the unit normal
@@ -217,6 +225,7 @@ typedef struct {
 } clbm_batch_item;
 
 /* Create a batch of n lattices in one device arena (two ping-pong buffers).
+ * Batched lattices run without the viscous source (viscous_heating must be 0).
  * autotune != 0 times the batched step with tile widths of 32, 64 and 128
  * nodes per warp for each class of row length (<= 48, <= 96, <= 192, > 192
  * nodes) and keeps the fastest; otherwise every lattice uses 128 (64 for

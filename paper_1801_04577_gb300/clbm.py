@@ -28,7 +28,8 @@ class clbm_params(C.Structure):
                 ("s_nu", C.c_double), ("s_b", C.c_double), ("s_3", C.c_double), ("s_4", C.c_double),
                 ("lambda0", C.c_double), ("lambda1", C.c_double), ("lambda2", C.c_double),
                 ("rho0", C.c_double), ("T0", C.c_double), ("gbeta", C.c_double),
-                ("Fvx", C.c_double), ("Fvy", C.c_double), ("Q", C.c_double), ("cT2", C.c_double)]
+                ("Fvx", C.c_double), ("Fvy", C.c_double), ("Q", C.c_double), ("cT2", C.c_double),
+                ("viscous_heating", C.c_int32), ("reserved1", C.c_int32)]
 
 
 class clbm_tbc(C.Structure):
@@ -139,7 +140,7 @@ def make_params(p, precision="f32", rounding: int = 0) -> clbm_params:
     prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     return clbm_params(p.nx, p.ny, p.periodic_x, p.periodic_y, prec, int(rounding), p.s_nu, p.s_b, p.s_3,
                        p.s_4, p.lambda0, p.lambda1, p.lambda2, p.rho0, p.T0, p.gbeta, p.Fvx,
-                       p.Fvy, p.Q, p.cT2)
+                       p.Fvy, p.Q, p.cT2, int(getattr(p, "viscous_heating", 0)), 0)
 
 
 # --------------------------------------------------------------------------

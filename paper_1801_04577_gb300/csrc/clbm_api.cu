@@ -137,6 +137,8 @@ static DevCoef make_coef(const clbm_ctx* c) {
   k.Fvy = c->p.Fvy;
   k.Q = c->p.Q;
   k.cT2 = c->p.cT2;
+  k.vh = c->p.viscous_heating ? 1 : 0;
+  k.pad = 0;
   return k;
 }
 
@@ -232,6 +234,7 @@ static clbm_status create_impl(const clbm_params* params, void* stream, void* bu
     return CLBM_EINVAL;
   auto rate_ok = [](double s) { return std::isfinite(s) && s > 0.0 && s < 2.0; };
   if (p.rounding != 0 && p.rounding != 1) return CLBM_EINVAL;
+  if (p.viscous_heating != 0 && p.viscous_heating != 1) return CLBM_EINVAL;
   if (!rate_ok(p.s_nu) || !rate_ok(p.s_b) || !rate_ok(p.s_4) || !rate_ok(p.lambda1) ||
       !(std::isfinite(p.lambda0)) || !(p.rho0 > 0) || !(p.cT2 > 0 && p.cT2 < 0.5))
     return CLBM_EINVAL;
@@ -247,7 +250,7 @@ static clbm_status create_impl(const clbm_params* params, void* stream, void* bu
   c->L = L;
   c->pitch = view_pitch(p.nx, p.precision);
   c->plane = (long long)p.ny * c->pitch;
-  c->buf_bytes = (size_t)14 * (size_t)c->plane * L->elem_bytes;
+  c->buf_bytes = (size_t)planes_of(p.viscous_heating) * (size_t)c->plane * L->elem_bytes;
   c->have_walls = p.periodic_x && p.periodic_y;
   for (int s = 0; s < 4; ++s)
     for (int k = 0; k < 3; ++k) c->side_b[s][k] = 0.0;
@@ -562,7 +565,8 @@ clbm_status clbm_step(clbm_ctx* c, int64_t nsteps) {
 clbm_status clbm_damp_period2(clbm_ctx* c) {
   if (!c) return CLBM_EINVAL;
   if (c->t < 1) return fail(c, CLBM_EINVAL, "needs one step after initialisation");
-  CLBM_CUDA(c, c->L->average(c->buf[c->cur], c->buf[c->cur ^ 1], 14 * c->plane, c->stream));
+  CLBM_CUDA(c, c->L->average(c->buf[c->cur], c->buf[c->cur ^ 1],
+                             planes_of(c->p.viscous_heating) * c->plane, c->stream));
   return CLBM_OK;
 }
 
@@ -722,10 +726,10 @@ int view_pitch(int nx, int precision) {
   return (nx + gran - 1) / gran * gran;
 }
 
-size_t view_buffer_bytes(int nx, int ny, int precision) {
+size_t view_buffer_bytes(int nx, int ny, int precision, int vh) {
   const Launchers* L = launchers_for(precision);
   if (!L) return 0;
-  return (size_t)14 * (size_t)ny * (size_t)view_pitch(nx, precision) * L->elem_bytes;
+  return (size_t)planes_of(vh) * (size_t)ny * (size_t)view_pitch(nx, precision) * L->elem_bytes;
 }
 
 clbm_status create_view(const clbm_params* p, cudaStream_t s, void* buf_a, void* buf_b,

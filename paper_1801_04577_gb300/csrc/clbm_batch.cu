@@ -302,7 +302,9 @@ clbm_status clbm_batch_create(const clbm_batch_item* items, int32_t n, int32_t a
                      : prec == CLBM_F16DEV ? &kLaunchF16 : prec == CLBM_BF16DEV ? &kLaunchBF16 : nullptr;
   if (!L) return CLBM_EINVAL;
   for (int i = 0; i < n; ++i)
-    if (items[i].params.precision != prec || items[i].params.rounding != rnd) return CLBM_EINVAL;
+    if (items[i].params.precision != prec || items[i].params.rounding != rnd ||
+        items[i].params.viscous_heating != 0)
+      return CLBM_EINVAL;
   clbm_batch* b = new (std::nothrow) clbm_batch();
   if (!b) return CLBM_ENOMEM;
   b->n = n;
@@ -328,7 +330,7 @@ clbm_status clbm_batch_create(const clbm_batch_item* items, int32_t n, int32_t a
     const clbm_params& p = items[i].params;
     if (p.nx < 1 || p.ny < 1 || p.ny > 65535) return bail(CLBM_EINVAL);
     off[i] = total;
-    total += (view_buffer_bytes(p.nx, p.ny, prec) + 255) / 256 * 256;
+    total += (view_buffer_bytes(p.nx, p.ny, prec, 0) + 255) / 256 * 256;
   }
   for (int k = 0; k < 2; ++k)
     if (cudaMalloc(&b->arena[k], total) != cudaSuccess) {

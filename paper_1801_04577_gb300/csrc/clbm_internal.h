@@ -17,6 +17,9 @@ namespace clbm {
 constexpr uint16_t kFlagSolid = 1u << 8;
 constexpr uint16_t kFlagLinks = 1u << 9;
 
+// Planes per buffer: 14 distributions, plus the viscous source Q_v when enabled.
+inline int planes_of(int vh) { return vh ? 15 : 14; }
+
 // Lattice geometry as seen by the kernels.  Distribution planes are stored
 // structure-of-arrays: plane q (f_0..f_8, then g_0..g_4) holds ny rows of
 // `pitch` elements, pitch = nx rounded up to a whole warp of vectors.
@@ -36,6 +39,8 @@ struct DevGeom {
 struct DevCoef {
   double s_nu, s_b, s3, s4, l0, l1, l2;
   double rho0, T0, gbeta, Fvx, Fvy, Q, cT2;
+  int vh;  // 1: viscous dissipation source (stored as a 15th plane, Q_v at each node)
+  int pad;
 };
 
 struct StepArgs {
@@ -105,7 +110,7 @@ struct Launchers {
                                 cudaStream_t s);
   // persistent grid size (blocks) of the batched interior step for V
   int (*batch_grid)(int V);
-  // a <- (a + b) / 2 over n stored values
+  // a <- (a + b) / 2 over n stored values (all planes)
   cudaError_t (*average)(void* a, const void* b, long long n, cudaStream_t s);
 
   // per-lattice residual: change of (T, ux, uy) since the previous check (snapshot), per step
@@ -131,7 +136,7 @@ struct ViewInfo {
   int nb;
 };
 int view_pitch(int nx, int precision);
-size_t view_buffer_bytes(int nx, int ny, int precision);
+size_t view_buffer_bytes(int nx, int ny, int precision, int vh);
 clbm_status create_view(const clbm_params* p, cudaStream_t s, void* buf_a, void* buf_b,
                         clbm_ctx** out);
 ViewInfo describe_view(const clbm_ctx* c);

@@ -209,6 +209,7 @@ struct Co {
   R rho0, T0, s_nu, s_b, s3, s4, l1, l2;
   R rgb;   // rho0 * g beta
   R Fvx, Fvy, Q, hQ, cT2;
+  R vhc;   // viscous source: Q_v = vhc (k~11^2 + (k~20 - k~02)^2 / 4) / rho^2
 };
 
 template <typename R>
@@ -228,6 +229,8 @@ __host__ __device__ __forceinline__ Co<R> make_co(const DevCoef& c) {
   o.Q = (R)c.Q;
   o.hQ = (R)(0.5 * c.Q);
   o.cT2 = (R)c.cT2;
+  // nu (D^2 + G^2) with G = -3 s_nu k~11/rho, D = -3 s_nu (k~20 - k~02)/(2 rho), nu = (1/s_nu - 1/2)/3
+  o.vhc = (R)(c.vh ? 3.0 * c.s_nu * c.s_nu * (1.0 / c.s_nu - 0.5) : 0.0);
   return o;
 }
 
@@ -254,8 +257,11 @@ __host__ __device__ __forceinline__ void inv1(R c0, R c1, R c2, R u, R& am, R& a
 // Collision of one node, on deviations.  In: pre-collision deviations d, h.
 // Out (in place): post-collision deviations.
 // ---------------------------------------------------------------------------
-template <typename R>
-__host__ __device__ __forceinline__ void collide(const Co<R>& c, R (&d)[9], R (&h)[5]) {
+// VH: add the viscous dissipation source Q_v (Sec. 3.2), read from the
+// pre-collision non-equilibrium central moments; it is returned in qv.  The
+// Boussinesq force uses T without Q_v/2 (Q_v needs u, which needs the force).
+template <typename R, bool VH = false>
+__host__ __device__ __forceinline__ void collide(const Co<R>& c, R (&d)[9], R (&h)[5], R& qv) {
   const R third = R(1.0 / 3.0);
   // Eq. 25 (T - T0 = sum h + Q/2) and Eq. 2
   const R sh = (h[0] + h[1]) + (h[2] + h[3]) + h[4];
@@ -300,6 +306,14 @@ __host__ __device__ __forceinline__ void collide(const Co<R>& c, R (&d)[9], R (&
   const R D12 = (R(1) - c.s3) * b12 + c.s3 * r0 * ux * (third + uy2) + hs3 * Fx;
   const R D22 = (R(1) - c.s4) * b22 - c.s4 * r0 * (third * (ux2 + uy2) + ux2 * uy2) +
                 c.s4 * R(1.0 / 9.0) * drho;
+  R Qt = c.Q;
+  qv = R(0);
+  if constexpr (VH) {
+    const R k11 = r0 * ux * uy + b11;
+    const R kd = r0 * (ux2 - uy2) + (b20 - b02);
+    qv = c.vhc * inv_rho * inv_rho * (k11 * k11 + R(0.25) * kd * kd);
+    Qt = c.Q + qv;
+  }
 
   // back-transformation: y-pass inverse per x-order, then x-pass inverse per row
   R ym0, yz0, yp0, ym1, yz1, yp1, ym2, yz2, yp2;
@@ -318,10 +332,11 @@ __host__ __device__ __forceinline__ void collide(const Co<R>& c, R (&d)[9], R (&
   const R t20 = k20 - (ux + ux) * k10 + ux2 * sh;
   const R t02 = k02 - (uy + uy) * k01 + uy2 * sh;
   const R T0 = c.T0;
-  const R E00 = sh + c.Q;
+  const R dTt = VH ? sh + R(0.5) * Qt : dT;  // Eq. 25 with the total source
+  const R E00 = sh + Qt;
   const R E10 = (R(1) - c.l1) * t10 + c.l1 * T0 * ux;
   const R E01 = (R(1) - c.l1) * t01 + c.l1 * T0 * uy;
-  const R src2 = (R(1) - R(0.5) * c.l2) * c.Q * c.cT2 + c.l2 * c.cT2 * dT;
+  const R src2 = (R(1) - R(0.5) * c.l2) * Qt * c.cT2 + c.l2 * c.cT2 * dTt;
   const R E20 = (R(1) - c.l2) * t20 - c.l2 * T0 * ux2 + src2;
   const R E02 = (R(1) - c.l2) * t02 - c.l2 * T0 * uy2 + src2;
   const R q10 = E10 + ux * E00, q01 = E01 + uy * E00;
@@ -332,6 +347,15 @@ __host__ __device__ __forceinline__ void collide(const Co<R>& c, R (&d)[9], R (&
   h[3] = R(0.5) * (q20 - q10);
   h[2] = R(0.5) * (q02 + q01);
   h[4] = R(0.5) * (q02 - q01);
+}
+
+template <typename R>
+__host__ __device__ __forceinline__ void collide_any(const Co<R>& c, bool vh, R (&d)[9], R (&h)[5],
+                                                     R& qv) {
+  if (vh)
+    collide<R, true>(c, d, h, qv);
+  else
+    collide<R, false>(c, d, h, qv);
 }
 
 // Pre-collision equilibrium deviations (central moments Eq. 9 and Eq. 19 minus
@@ -376,14 +400,17 @@ __host__ __device__ __forceinline__ R wall_temperature(R b1, R b2, R b3, R ne, R
   return (R(2) * b1 * T1 + ne * b3) / (R(2) * b1 + ne * b2);
 }
 
-// T at a node from its post-collision thermal deviations: T = T0 + sum h* - Q/2.
+// T at a node from its post-collision thermal deviations: T = T0 + sum h* - Q/2,
+// Q including the node's stored viscous source when that is enabled.
 template <typename S, typename R>
 __device__ __forceinline__ R node_T(const S* __restrict__ src, long long plane, long long idx,
                                     const Co<R>& c) {
   R s = to_r(src[9 * plane + idx]);
 #pragma unroll
   for (int q = 10; q < 14; ++q) s += to_r(src[q * plane + idx]);
-  return c.T0 + s - c.hQ;
+  R t = c.T0 + s - c.hQ;
+  if (c.vhc != R(0)) t -= R(0.5) * to_r(src[14 * plane + idx]);
+  return t;
 }
 
 // Fix-up of one node that touches a wall, a periodic seam or a solid.
@@ -475,7 +502,7 @@ __device__ __forceinline__ void st1(S* p, R v, int stochastic, uint32_t r) {
 // next to solids come out wrong here and are recomputed afterwards by the
 // boundary kernel from its precomputed node list.  Keeping the walls out of
 // this kernel keeps its warps free of divergent wall code.
-template <typename S, int V, bool SKIP_EDGES = false>
+template <typename S, int V, bool SKIP_EDGES = false, bool VH = false>
 __device__ __forceinline__ void step_tile(const DevGeom& g, const Co<typename Traits<S>::R>& c,
                                           const S* __restrict__ src, S* __restrict__ dst, int y,
                                           int xw, int lane, uint32_t seed, int stochastic) {
@@ -521,6 +548,7 @@ __device__ __forceinline__ void step_tile(const DevGeom& g, const Co<typename Tr
     }
   }
 
+  R qv[V];
 #pragma unroll
   for (int k = 0; k < V; ++k) {
     R d[9], h[5];
@@ -528,7 +556,7 @@ __device__ __forceinline__ void step_tile(const DevGeom& g, const Co<typename Tr
     for (int q = 0; q < 9; ++q) d[q] = v[q][k];
 #pragma unroll
     for (int q = 0; q < 5; ++q) h[q] = v[9 + q][k];
-    collide(c, d, h);
+    collide<R, VH>(c, d, h, qv[k]);
 #pragma unroll
     for (int q = 0; q < 9; ++q) v[q][k] = d[q];
 #pragma unroll
@@ -536,6 +564,17 @@ __device__ __forceinline__ void step_tile(const DevGeom& g, const Co<typename Tr
   }
 
   S* out = dst + (long long)y * g.pitch + x0;
+  if constexpr (VH) {  // the viscous source of this step, read back with T (15th plane)
+    if constexpr (SKIP_EDGES) {
+#pragma unroll
+      for (int k = 0; k < V; ++k) {
+        const int x = x0 + k;
+        if (x != 0 && x != g.nx - 1) out[14 * plane + k] = from_r<S, R>(qv[k]);
+      }
+    } else {
+      stv<S, V>(out + 14 * plane, qv);
+    }
+  }
   if constexpr (SKIP_EDGES) {
     // leave the first and last column to the boundary update running alongside
     if (x0 == 0 || (x0 <= g.nx - 1 && g.nx - 1 < x0 + V)) {
@@ -592,7 +631,10 @@ __device__ __forceinline__ void step_node(const DevGeom& g, const Co<typename Tr
   }
   const uint16_t fl = MASK ? g.flags[i] : (uint16_t)0;
   fixup<S, MASK>(g, c, src, x, y, fl, d, h);
-  collide(c, d, h);
+  R qv;
+  const bool vh = c.vhc != R(0);
+  collide_any(c, vh, d, h, qv);
+  if (vh) dst[14 * plane + i] = from_r<S, R>(qv);
   const uint32_t key = seed ^ mix32((uint32_t)i);
 #pragma unroll
   for (int q = 0; q < 14; ++q) {
@@ -611,7 +653,7 @@ __device__ __forceinline__ uint32_t step_seed(const StepArgs& a) {
 }
 
 // One launch = the interior update of one time step of one lattice.
-template <typename S>
+template <typename S, bool VH>
 __global__ void __launch_bounds__(kStepThreads) step_kernel(const StepArgs a) {
   using R = typename Traits<S>::R;
   constexpr int V = Traits<S>::V;
@@ -621,8 +663,8 @@ __global__ void __launch_bounds__(kStepThreads) step_kernel(const StepArgs a) {
   if (xw >= a.g.nx) return;  // whole warps only: the shuffles need all 32 lanes
   const Co<R> c = make_co<R>(a.c);
   const int y = a.reverse ? a.g.ny - 1 - (int)blockIdx.y : (int)blockIdx.y;
-  step_tile<S, V>(a.g, c, static_cast<const S*>(a.src), static_cast<S*>(a.dst), y, xw, lane,
-                  step_seed(a), a.stochastic);
+  step_tile<S, V, false, VH>(a.g, c, static_cast<const S*>(a.src), static_cast<S*>(a.dst), y, xw,
+                             lane, step_seed(a), a.stochastic);
 }
 
 // The boundary nodes of the same step (launched after step_kernel).
@@ -642,7 +684,7 @@ __global__ void __launch_bounds__(kRedThreads) boundary_kernel(const StepArgs a)
 // interior tiles of rows that are not boundary rows, which skip the first and
 // last column.  The latency-bound boundary work then overlaps the streaming
 // interior work instead of following it.
-template <typename S>
+template <typename S, bool VH>
 __global__ void __launch_bounds__(kStepThreads, 5) step_fused_kernel(const StepArgs a, int nbb,
                                                                   int xblocks, int y0) {
   using R = typename Traits<S>::R;
@@ -663,8 +705,8 @@ __global__ void __launch_bounds__(kStepThreads, 5) step_fused_kernel(const StepA
   const int warp = (b % xblocks) * (kStepThreads / 32) + (threadIdx.x >> 5);
   const int xw = warp * 32 * V;
   if (xw >= a.g.nx) return;  // whole warps only
-  step_tile<S, V, true>(a.g, c, static_cast<const S*>(a.src), static_cast<S*>(a.dst), y, xw, lane,
-                        step_seed(a), a.stochastic);
+  step_tile<S, V, true, VH>(a.g, c, static_cast<const S*>(a.src), static_cast<S*>(a.dst), y, xw,
+                            lane, step_seed(a), a.stochastic);
 }
 
 // ---------------------------------------------------------------------------
@@ -691,8 +733,11 @@ __global__ void init_kernel(const DevGeom g, const DevCoef cf, S* __restrict__ d
       const R w = uy ? (R)uy[k] : R(0);
       const R t = T ? (R)T[k] : c.T0;
       equilibrium(c, r, u, w, t, d, h);
-      collide(c, d, h);
+      R qv;
+      collide_any(c, cf.vh != 0, d, h, qv);
+      if (cf.vh) dst[14 * g.plane + i] = from_r<S, R>(qv);
     } else {
+      if (cf.vh) dst[14 * g.plane + i] = from_r<S, R>(R(0));
 #pragma unroll
       for (int q = 0; q < 9; ++q) d[q] = R(0);
 #pragma unroll
@@ -719,8 +764,10 @@ __device__ __forceinline__ void node_macros(const DevCoef& c, const S* __restric
   for (int q = 0; q < 9; ++q) f[q] = (double)to_r(b[q * plane + i]);
 #pragma unroll
   for (int q = 9; q < 14; ++q) s += (double)to_r(b[q * plane + i]);
-  T = c.T0 + s - 0.5 * c.Q;
-  const double Fx = c.Fvx, Fy = c.Fvy + c.rho0 * c.gbeta * (T - c.T0);
+  const double qv = c.vh ? (double)to_r(b[14 * plane + i]) : 0.0;
+  T = c.T0 + s - 0.5 * (c.Q + qv);
+  // the Boussinesq force uses T without the viscous source's half
+  const double Fx = c.Fvx, Fy = c.Fvy + c.rho0 * c.gbeta * (T - 0.5 * qv - c.T0);
   const double dr = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
   rho = c.rho0 + dr;
   const double jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
@@ -830,7 +877,7 @@ __global__ void __launch_bounds__(kRedThreads)
 // lattice, row, x), so it stays on one lattice for many tiles; the lattice's
 // descriptor is copied into a per-warp shared-memory slot when it changes and
 // read from there, instead of chasing it through global memory on every tile.
-template <typename S, int V>
+template <typename S, int V, bool VH>
 __global__ void __launch_bounds__(kStepThreads, 4)
     batch_step_kernel(const BatchLat* __restrict__ lats, const int4* __restrict__ tiles,
                       const int* __restrict__ count, int parity, const long long* __restrict__ tptr,
@@ -864,8 +911,9 @@ __global__ void __launch_bounds__(kStepThreads, 4)
       cur = tl.x;
       c = make_co<R>(L.c);
     }
-    step_tile<S, V>(L.g, c, static_cast<const S*>(L.buf[parity]),
-                    static_cast<S*>(L.buf[parity ^ 1]), tl.y, tl.z, lane, seed, stochastic);
+    step_tile<S, V, false, VH>(L.g, c, static_cast<const S*>(L.buf[parity]),
+                               static_cast<S*>(L.buf[parity ^ 1]), tl.y, tl.z, lane, seed,
+                               stochastic);
   }
 }
 
@@ -978,12 +1026,18 @@ struct LaunchImpl {
       const int nbb = (a.nb + kStepThreads - 1) / kStepThreads;
       const long long blocks = (long long)nbb + (long long)xblocks * rows;
       if (blocks > 0 && blocks < (1LL << 31)) {
-        step_fused_kernel<S><<<(unsigned)blocks, kStepThreads, 0, s>>>(a, nbb, xblocks, y0);
+        if (a.c.vh)
+          step_fused_kernel<S, true><<<(unsigned)blocks, kStepThreads, 0, s>>>(a, nbb, xblocks, y0);
+        else
+          step_fused_kernel<S, false><<<(unsigned)blocks, kStepThreads, 0, s>>>(a, nbb, xblocks, y0);
         return cudaGetLastError();
       }
     }
     dim3 grid(xblocks, a.g.ny);
-    step_kernel<S><<<grid, kStepThreads, 0, s>>>(a);
+    if (a.c.vh)
+      step_kernel<S, true><<<grid, kStepThreads, 0, s>>>(a);
+    else
+      step_kernel<S, false><<<grid, kStepThreads, 0, s>>>(a);
     if (a.nb > 0) {
       const int blocks = (a.nb + kRedThreads - 1) / kRedThreads;
       if (a.g.flags)
@@ -1035,8 +1089,9 @@ struct LaunchImpl {
   static cudaError_t batch_launch(const BatchLat* lats, const int4* tiles, const int* count,
                                   int parity, const long long* t, int tstep, int stochastic, int grid,
                                   cudaStream_t s) {
-    batch_step_kernel<S, VV><<<grid, kStepThreads, 0, s>>>(lats, tiles, count, parity, t, tstep,
-                                                            stochastic);
+    // batches run without the viscous source (clbm_batch_create rejects it)
+    batch_step_kernel<S, VV, false><<<grid, kStepThreads, 0, s>>>(lats, tiles, count, parity, t,
+                                                                   tstep, stochastic);
     return cudaGetLastError();
   }
 
@@ -1067,7 +1122,7 @@ struct LaunchImpl {
     int per_sm = 0, dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_step_kernel<S, VV>,
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_step_kernel<S, VV, false>,
                                                       kStepThreads, 0) != cudaSuccess)
       return 0;
     return sms * (per_sm > 0 ? per_sm : 1);

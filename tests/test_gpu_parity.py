@@ -180,3 +180,34 @@ def test_graph_replay_matches_single_launches(precision, rounding, name):
     assert a.time == b.time == 73
     for x, y in zip(a.moments(), b.moments()):
         np.testing.assert_array_equal(x, y)
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+@pytest.mark.parametrize("name", ["cavity", "obstacle"])
+def test_viscous_heating_matches_oracle(precision, name):
+    """Viscous dissipation source (Sec. 3.2) on a box lattice (fused launch) and
+    on a masked one with source, force and mixed walls."""
+    w = I.natural_convection_cavity(48, 1e4) if name == "cavity" else I.obstacle_channel()
+    w.params.viscous_heating = 1
+    if name == "cavity":
+        w.params.Fvx = 2e-5  # stronger shear so the source matters
+    errs, (s, o) = run_pair(w, 600, precision)
+    _assert_within(errs, TOL[precision], f"viscous {name} {precision}")
+    a, b = s.nusselt(0, w.length, 1.0), o.nusselt(0, w.length, 1.0)
+    assert abs(a - b) <= (1e-11 if precision == "f64" else 1e-4) * max(1.0, abs(b))
+
+
+def test_viscous_heating_channel_profile_gpu():
+    """Sec. 3.2 on the GPU: the steady channel temperature matches the exact
+    quartic profile as closely as the oracle does (E2 ~ 7e-3 at L = 16)."""
+    L, nu, alpha, Fx = 16, 0.1, 0.1, 1e-5
+    w = I.dissipation_channel(L, nu, alpha, Fx, nx=64)
+    s = clbm.from_workload(w, "f64")
+    s.step(int(20 * L * L / alpha) + 2000)
+    T = s.moments()[3]
+    Ta = I.dissipation_exact(L, nu, alpha, Fx)
+    E2 = np.sqrt(((T - Ta[:, None]) ** 2).sum(axis=0) / (Ta ** 2).sum())
+    assert E2.max() < 1e-2
+    o = oracle.from_workload(I.dissipation_channel(L, nu, alpha, Fx, nx=1))
+    o.step(int(20 * L * L / alpha) + 2000)
+    np.testing.assert_allclose(T[:, 0], o.moments()[3][:, 0], rtol=1e-10, atol=1e-18)
