@@ -43,9 +43,9 @@ DTYPE = {"f64": "f64", "f32": "f32", "f16": "f16-storage/f32-compute", "bf16": "
 # workload, valid only for the kernel source whose SHA-256 prefix is stored.
 NCU_TRAFFIC = {
     # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum (1 pass) on the full 4096 x 2048
-    # lattice, three launches of step_fused_kernel<float>: 479.3 MB read + 418.0 MB written
+    # lattice, three launches of step_fused_kernel<float>: 479.3 MB read + 417.9 MB written
     # (the rest of the written lines is still dirty in L2 when the launch ends).
-    "f32:rb4096": {"bytes_per_launch": 897.4e6, "kernel_hash": "6ce37ccdac578171"},
+    "f32:rb4096": {"bytes_per_launch": 897.2e6, "kernel_hash": "ed895c9ffcffae02"},
 }
 
 
@@ -232,6 +232,30 @@ def combine_ranks(elapsed_ms: float, nodes: int, steps: int, device=None):
     return el, world * nodes * steps / (el * 1e-3) / 1e6
 
 
+def box_lattice(w) -> bool:
+    """No solid mask and no listed links: the library fuses interior and
+    boundary work into one launch per step."""
+    return w.geom.solid is None and len(w.geom.link_node) == 0
+
+
+def step_kernel_name(w) -> str:
+    if box_lattice(w):
+        return "step_fused_kernel (interior tiles + boundary nodes, one launch per step)"
+    return "step_kernel + boundary_kernel (two launches per step)"
+
+
+def step_launches(w, steps: int, graph_steps: int = 32) -> int:
+    """Kernels that clbm_step(steps) launches: per step one fused launch (box
+    lattices) or the interior and boundary kernels; runs of graph_steps or more
+    replay a captured graph that adds one step-counter kernel per graph, after
+    one kernel that sets the counter."""
+    per_step = 1 if box_lattice(w) else 2
+    n = per_step * steps
+    if steps >= graph_steps:
+        n += 1 + steps // graph_steps
+    return n
+
+
 def run_native(args):
     import torch
     import torch.distributed as dist
@@ -323,10 +347,10 @@ def run_native(args):
                            parallelism=f"replicas{world}" if world > 1 else "single"),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
-                         "kernel": "clbm::step_kernel + clbm::boundary_kernel (one step)",
+                         "kernel": step_kernel_name(w),
                          "peak_kind": peak_kind,
                          "algorithmic_bytes_per_launch": bytes_lu * nodes},
-            "gpu_launches": 2 * args.steps,  # interior + boundary kernel per step
+            "gpu_launches": step_launches(w, args.steps),
             "residual_after": res}
     if e2e is not None:
         line["e2e"] = e2e

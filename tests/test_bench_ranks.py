@@ -48,3 +48,15 @@ def test_single_process_has_no_collective():
     import bench
     el, mlups = bench.combine_ranks(5.0, nodes=100, steps=10)
     assert el == 5.0 and mlups == pytest.approx(100 * 10 / 5e-3 / 1e6)
+
+
+def test_launch_count_claim_follows_the_launch_scheme():
+    """gpu_launches: one fused launch per step on box lattices, two on masked
+    ones, plus the graph's step-counter kernels for runs of 32 steps or more."""
+    import bench
+    rb = bench.workload("rb256")
+    an = bench.workload("annulus2048")
+    assert bench.box_lattice(rb) and not bench.box_lattice(an)
+    assert bench.step_launches(rb, 10) == 10
+    assert bench.step_launches(rb, 64) == 64 + 1 + 2
+    assert bench.step_launches(an, 100) == 200 + 1 + 3
