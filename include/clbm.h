@@ -272,11 +272,26 @@ const char* clbm_batch_last_error(const clbm_batch* b);
  *   levels L (2..6), base width B: widths B, 2B, ..., 2^(L-1) B; G must be
  *   divisible by 2^(L-1).  Input in_ch, output out_ch channels (NCHW FP32).
  * All tensors passed to these calls are FP32 device arrays.
+ *
+ * Convolution arithmetic (clbm_net_config.math):
+ *   CLBM_NET_TENSOR  5th-generation tensor cores (tcgen05.mma): both GEMM
+ *                    operands (activations or activation gradients, and
+ *                    weights) rounded to BF16 (nearest even), products
+ *                    accumulated in FP32 in tensor memory.
+ *   CLBM_NET_FP32    FP32 CUDA cores: FP32 activations and gradients, BF16
+ *                    weights, FP32 accumulation.
+ * Bias, pooling, upsampling, ReLU, loss and Adam are FP32 in both.  A
+ * tensor-core GEMM that waits more than about a second for its MMAs gives
+ * up, and the next clbm_net_forward / clbm_net_gradients /
+ * clbm_net_train_step returns CLBM_ETIMEOUT (sticky for the network).
  * ------------------------------------------------------------------- */
 typedef struct clbm_net clbm_net;
 
+typedef enum { CLBM_NET_TENSOR = 0, CLBM_NET_FP32 = 1 } clbm_net_math;
+
 typedef struct {
   int32_t grid, in_ch, out_ch, base, levels, max_batch;
+  int32_t math; /* clbm_net_math; any other value: CLBM_EINVAL */
 } clbm_net_config;
 
 /* Create a network with seeded He-uniform weights and zero biases. */

@@ -10,8 +10,11 @@
 // Activations are FP32 NCHW; weights are kept as an FP32 master copy (Adam)
 // and a BF16 copy that every convolution reads; accumulation is FP32.
 //
-// Every convolution pass is one implicit GEMM (gemm_kernel) with on-the-fly
-// im2col loaders:
+// Every convolution pass is one implicit GEMM with on-the-fly im2col loaders,
+// run either on the tensor cores (tc::gemm_kernel in clbm_tc.cuh: both
+// operands rounded to BF16 as they are staged in shared memory, tcgen05.mma,
+// FP32 accumulator in TMEM; the default) or on the FP32 CUDA cores
+// (gemm_kernel below: FP32 activations, BF16 weights):
 //   forward      Y[co, p]      = sum_{ci,t} W[co, ci t] X[ci, p + t]
 //   input grad   dX[ci, p]    += sum_{co,t} W'[ci, co t] dY[co, p + t]   (W' = W flipped, transposed)
 //   weight grad  dW[co, ci t]  = sum_p dY[co, p] X[ci, p + t]          (split-K over pixels,
@@ -29,6 +32,7 @@
 #include <vector>
 
 #include "../../include/clbm.h"
+#include "clbm_tc.cuh"
 
 namespace {
 
@@ -118,6 +122,181 @@ struct StorePartial {
     part[((long long)split * M + m) * N + n] = v;
   }
 };
+
+// ---------------------------------------------------------------------------
+// Operands of the tensor-core GEMM (rows m of D are TMEM lanes): the
+// convolutions put pixels on m for the forward and input-gradient passes, and
+// (channel, tap) pairs on m for the weight gradient.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void put_chunk(uint8_t* dst, int r, int kc, const float (&v)[8]) {
+  *reinterpret_cast<uint4*>(dst + tc::chunk_off(r, kc)) =
+      make_uint4(tc::pack_bf16(v[0], v[1]), tc::pack_bf16(v[2], v[3]), tc::pack_bf16(v[4], v[5]),
+                 tc::pack_bf16(v[6], v[7]));
+}
+
+// A(m = pixel, k = (channel, tap)) = x[channel] at pixel + tap offset (zero
+// outside the image): thread r gathers row r, so every load of a warp reads
+// 32 consecutive pixels.
+template <int KS>
+struct GatherIm2col {
+  static constexpr bool kBulk = false;
+  Act x;
+  __device__ __forceinline__ void operator()(uint8_t* dst, int row0, int rows_valid, int, int k0,
+                                             int kend) const {
+    constexpr int KK = KS * KS, R = KS / 2;
+    const int r = threadIdx.x;
+    const int hw = x.H * x.W;
+    const bool rv = r < rows_valid;
+    int nb = 0, p = 0, yy = 0, xx = 0;
+    if (rv) {
+      const int m = row0 + r;
+      nb = m / hw;
+      p = m - nb * hw;
+      yy = p / x.W;
+      xx = p - yy * x.W;
+    }
+    const float* src = x.base + ((long long)nb * x.cs + x.coff) * hw + p;
+    uint32_t vm = 0;  // taps inside the image
+#pragma unroll
+    for (int t = 0; t < KK; ++t) {
+      const int sy = yy + t / KS - R, sx = xx + t % KS - R;
+      if (rv && sy >= 0 && sy < x.H && sx >= 0 && sx < x.W) vm |= 1u << t;
+    }
+    int c = k0 / KK, t = k0 - c * KK;
+#pragma unroll
+    for (int kc = 0; kc < tc::kBK / 8; ++kc) {
+      float v[8];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const int k = k0 + kc * 8 + e;
+        const int off = (t / KS - R) * x.W + (t % KS - R);
+        v[e] = (k < kend && ((vm >> t) & 1u)) ? __ldg(src + c * hw + off) : 0.0f;
+        if (++t == KK) {
+          t = 0;
+          ++c;
+        }
+      }
+      put_chunk(dst, r, kc, v);
+    }
+  }
+};
+
+// A(m = (channel, tap), k = pixel) = x[channel] at pixel + tap offset: eight
+// consecutive threads gather the 64 pixels of one row, 8 each.
+template <int KS>
+struct GatherIm2colT {
+  static constexpr bool kBulk = false;
+  Act x;
+  __device__ __forceinline__ void operator()(uint8_t* dst, int row0, int rows_valid, int, int k0,
+                                             int kend) const {
+    constexpr int KK = KS * KS, R = KS / 2;
+    const int hw = x.H * x.W;
+    for (int task = threadIdx.x; task < tc::kBM * 8; task += tc::kThreads) {
+      const int r = task >> 3, kc = task & 7;
+      const int row = row0 + r;
+      const int c = row / KK, t = row - c * KK;
+      const int dy = t / KS - R, dx = t % KS - R;
+      const int k = k0 + kc * 8;
+      int nb = k / hw, p = k - nb * hw;
+      int yy = p / x.W, xx = p - yy * x.W;
+      float v[8];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const int sy = yy + dy, sx = xx + dx;
+        const bool ok = r < rows_valid && k + e < kend && sy >= 0 && sy < x.H && sx >= 0 && sx < x.W;
+        v[e] = ok ? __ldg(x.base + ((long long)nb * x.cs + x.coff + c) * hw + sy * x.W + sx) : 0.0f;
+        if (++xx == x.W) {
+          xx = 0;
+          if (++yy == x.H) {
+            yy = 0;
+            ++nb;
+          }
+        }
+      }
+      put_chunk(dst, r, kc, v);
+    }
+  }
+};
+
+// B(n = channel, k = pixel) = g[channel][pixel] of an activation(-gradient)
+// view: eight consecutive threads read one row's 64 pixels (two float4 each
+// when a sample's pixel count is a multiple of 8).
+struct GatherRows {
+  static constexpr bool kBulk = false;
+  Act a;
+  __device__ __forceinline__ void operator()(uint8_t* dst, int row0, int rows_valid, int nrows, int k0,
+                                             int kend) const {
+    const int hw = a.H * a.W;
+    const bool vec = (hw & 7) == 0;
+    for (int task = threadIdx.x; task < nrows * 8; task += tc::kThreads) {
+      const int r = task >> 3, kc = task & 7;
+      const int k = k0 + kc * 8;
+      const long long ch = a.coff + row0 + r;
+      float v[8];
+      if (r < rows_valid && vec && k + 8 <= kend) {
+        const int nb = k / hw, p = k - nb * hw;
+        const float4* s4 = reinterpret_cast<const float4*>(a.base + ((long long)nb * a.cs + ch) * hw + p);
+        const float4 u0 = __ldg(s4), u1 = __ldg(s4 + 1);
+        v[0] = u0.x; v[1] = u0.y; v[2] = u0.z; v[3] = u0.w;
+        v[4] = u1.x; v[5] = u1.y; v[6] = u1.z; v[7] = u1.w;
+      } else {
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          const int kk = k + e;
+          const int nb = kk / hw, p = kk - nb * hw;
+          v[e] = (r < rows_valid && kk < kend) ? __ldg(a.base + ((long long)nb * a.cs + ch) * hw + p) : 0.0f;
+        }
+      }
+      put_chunk(dst, r, kc, v);
+    }
+  }
+};
+
+struct TStoreAct {  // D(m = pixel, n = channel)
+  StoreAct s;
+  __device__ __forceinline__ void operator()(int m, int n, float v, int) const { s(n, m, v); }
+};
+struct TStorePartial {  // D(m = (ci, tap), n = co) of split z
+  StorePartial s;
+  __device__ __forceinline__ void operator()(int m, int n, float v, int z) const { s(n, m, v, z); }
+};
+
+// Pre-packed BF16 weights for the tensor-core GEMMs (tc::Packed layout), one
+// entry per layer and direction: forward B(n = co, k = (ci, tap)) = W, input
+// gradient B(n = ci, k = (co, tap')) = W with the taps flipped.
+struct PackDesc {
+  long long w_off;    // layer weights in the parameter vector
+  long long dst_off;  // first element of this layer's packed buffer
+  int co, ci, kk;     // output / input channels, taps
+  int transpose;      // 0: forward, 1: input gradient
+  int N, K, bn, slices;
+  long long size;     // packed elements (N tiles x slices x bn x 64)
+};
+
+__global__ void pack_weights_kernel(const PackDesc* __restrict__ descs, const __nv_bfloat16* __restrict__ w,
+                                    __nv_bfloat16* __restrict__ out) {
+  const PackDesc d = descs[blockIdx.y];
+  const long long tile_e = (long long)d.bn * tc::kBK;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < d.size;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long tile = i / tile_e;
+    const int within = (int)(i - tile * tile_e);
+    const int nt = (int)(tile / d.slices), ks = (int)(tile - (long long)nt * d.slices);
+    // inverse of chunk_off: 512 elements per 8-row group, 64 per K chunk, 8 per row
+    const int rg = within >> 9, kc = (within >> 6) & 7, r7 = (within >> 3) & 7, e = within & 7;
+    const int n = nt * d.bn + rg * 8 + r7, k = ks * tc::kBK + kc * 8 + e;
+    __nv_bfloat16 v = __float2bfloat16_rn(0.0f);
+    if (n < d.N && k < d.K) {
+      if (!d.transpose) {
+        v = w[d.w_off + (long long)n * d.K + k];
+      } else {  // n = ci, k = (co, t'): W[co][ci][kk - 1 - t']
+        const int co = k / d.kk, tp = k - co * d.kk;
+        v = w[d.w_off + ((long long)co * d.ci + n) * d.kk + (d.kk - 1 - tp)];
+      }
+    }
+    out[d.dst_off + i] = v;
+  }
+}
 
 // ---------------------------------------------------------------------------
 // Tiled FP32 GEMM: 64 x 64 output tile per block, 4 x 4 per thread, K in
@@ -339,7 +518,7 @@ int grid1(long long n) {
 }
 
 struct Conv {  // one convolution layer
-  int ci, co, ks, H, W;
+  int index, ci, co, ks, H, W;
   long long w_off, b_off;  // offsets in the parameter vector (weights, then bias)
 };
 
@@ -361,11 +540,17 @@ struct clbm_net {
   long long nparam = 0;
   float *p = nullptr, *g = nullptr, *m = nullptr, *v = nullptr;
   __nv_bfloat16 *pb = nullptr, *pt = nullptr;  // BF16 weights and flipped copy
+  __nv_bfloat16* packed = nullptr;             // tensor-core weight tiles (PackDesc layout)
+  PackDesc* d_pack = nullptr;
+  std::vector<PackDesc> pack;                  // [2 * layer + transpose]
+  long long packed_max = 0;
   std::vector<float*> act, gact;               // per buffer
   std::vector<int> act_c, act_hw;              // channels and H (= W) of each buffer
   float* part = nullptr;                       // split-K partials
   long long part_cap = 0;
   double* loss_part = nullptr;
+  int* tflag = nullptr;  // mapped pinned host flag: a tensor-core wait timed out
+  int* d_tflag = nullptr;
   int64_t steps = 0;
   Plan plan{};
   std::string err;
@@ -410,12 +595,57 @@ Act view(clbm_net* net, int id, int coff, int C, bool grad = false) {
   return a;
 }
 
+bool tensor_math(const clbm_net* net) { return net->cfg.math == CLBM_NET_TENSOR; }
+
+// D[M][N] (+ split-K along z) on the tensor cores
+template <class GA, class GB, class ST>
+cudaError_t tc_gemm(clbm_net* net, GA ga, GB gb, ST st, int M, int N, int K, int kper) {
+  const int bn = tc::tile_n(N);
+  auto kern = tc::gemm_kernel<GA, GB, ST>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       tc::smem_bytes(tc::kMaxBN));
+  if (e) return e;
+  dim3 grid((M + tc::kBM - 1) / tc::kBM, (N + bn - 1) / bn, (K + kper - 1) / kper);
+  kern<<<grid, tc::kThreads, tc::smem_bytes(bn), net->stream>>>(ga, gb, st, M, N, K, kper, bn, net->d_tflag);
+  return cudaGetLastError();
+}
+
+// Refresh the packed weight tiles from the BF16 weights (one launch, all layers).
+cudaError_t pack_weights(clbm_net* net) {
+  if (!tensor_math(net)) return cudaSuccess;
+  dim3 grid((unsigned)std::min<long long>((net->packed_max + 255) / 256, 1024), (unsigned)net->pack.size());
+  pack_weights_kernel<<<grid, 256, 0, net->stream>>>(net->d_pack, net->pb, net->packed);
+  return cudaGetLastError();
+}
+
+tc::Packed packed_of(const clbm_net* net, int layer, int transpose) {
+  const PackDesc& d = net->pack[2 * layer + transpose];
+  return tc::Packed{net->packed + d.dst_off, d.slices};
+}
+
+// K range per split of a weight-gradient GEMM (K = pixels): the FP32 kernel
+// takes 4096 pixels per split; the tensor-core one enough splits to give
+// about two CTAs per SM (a multiple of its 64-wide K slice).
+long long dw_kper(bool tensor, long long Np, int Kd, int co) {
+  if (!tensor) return 4096;
+  const long long tiles = (long long)((Kd + tc::kBM - 1) / tc::kBM) * ((co + tc::kMaxBN - 1) / tc::kMaxBN);
+  long long splits = std::max<long long>(1, (2 * 152 + tiles - 1) / tiles);
+  splits = std::min<long long>(splits, std::max<long long>(1, Np / 512));
+  const long long per = (Np + splits - 1) / splits;
+  return ((per + tc::kBK - 1) / tc::kBK) * tc::kBK;
+}
+
 cudaError_t conv_forward(clbm_net* net, const Conv& cv, Act x, int out_id, int out_coff, int relu,
                          int N) {
   const int M = cv.co, Kd = cv.ci * cv.ks * cv.ks, Np = N * cv.H * cv.W;
   LoadW la{net->pb + cv.w_off, Kd};
   LoadIm2col lb{x, cv.ks};
   StoreAct st{net->act[out_id], net->act_c[out_id], out_coff, cv.H, cv.W, net->p + cv.b_off, relu, 0};
+  if (tensor_math(net)) {  // D(pixel, co) = sum_k im2col(x)(pixel, k) W(co, k)
+    const tc::Packed w = packed_of(net, cv.index, 0);
+    if (cv.ks == 3) return tc_gemm(net, GatherIm2col<3>{x}, w, TStoreAct{st}, Np, M, Kd, Kd);
+    return tc_gemm(net, GatherIm2col<1>{x}, w, TStoreAct{st}, Np, M, Kd, Kd);
+  }
   dim3 grid((Np + BN - 1) / BN, (M + BM - 1) / BM, 1);
   gemm_kernel<<<grid, GT, 0, net->stream>>>(la, lb, st, M, Np, Kd, Kd);
   return cudaGetLastError();
@@ -428,26 +658,40 @@ cudaError_t conv_backward(clbm_net* net, const Conv& cv, Act x, Act gy, int gx_i
   const int Kd = cv.ci * cv.ks * cv.ks, Np = N * cv.H * cv.W;
   // weight gradient: M = co, N = ci*t, K = pixels, split-K
   {
-    const int kper = 4096;
+    const bool tensor = tensor_math(net);
+    const int kper = (int)dw_kper(tensor, Np, Kd, cv.co);
     const int splits = (Np + kper - 1) / kper;
     const long long need = (long long)splits * cv.co * Kd;
     if (need > net->part_cap) return cudaErrorInvalidValue;
     LoadActMK la{gy};
     LoadIm2colT lb{x, cv.ks};
     StorePartial st{net->part, cv.co, Kd};
-    dim3 grid((Kd + BN - 1) / BN, (cv.co + BM - 1) / BM, splits);
-    gemm_kernel<<<grid, GT, 0, net->stream>>>(la, lb, st, cv.co, Kd, Np, kper);
+    if (tensor) {  // D((ci, t), co) = sum_p im2col(x)(p, (ci, t)) gy(co, p)
+      cudaError_t e = cv.ks == 3
+                          ? tc_gemm(net, GatherIm2colT<3>{x}, GatherRows{gy}, TStorePartial{st}, Kd, cv.co, Np, kper)
+                          : tc_gemm(net, GatherIm2colT<1>{x}, GatherRows{gy}, TStorePartial{st}, Kd, cv.co, Np, kper);
+      if (e) return e;
+    } else {
+      dim3 grid((Kd + BN - 1) / BN, (cv.co + BM - 1) / BM, splits);
+      gemm_kernel<<<grid, GT, 0, net->stream>>>(la, lb, st, cv.co, Kd, Np, kper);
+    }
     const long long n = (long long)cv.co * Kd;
     sum_splits_kernel<<<grid1(n), 256, 0, net->stream>>>(net->part, splits, n, net->g + cv.w_off);
     bias_grad_kernel<<<cv.co, GT, 0, net->stream>>>(gy, N, net->g + cv.b_off);
   }
   if (gx_id >= 0) {  // input gradient: M = ci, N = pixels, K = co*t, with flipped weights
     const int kk = cv.ks * cv.ks;
+    StoreAct st{net->gact[gx_id], net->act_c[gx_id], gx_coff, cv.H, cv.W, nullptr, 0, 1};
+    if (tensor_math(net)) {  // D(pixel, ci) = sum_k im2col(gy)(pixel, k) W'(ci, k)
+      const tc::Packed w = packed_of(net, cv.index, 1);
+      const int K = cv.co * kk;
+      if (cv.ks == 3) return tc_gemm(net, GatherIm2col<3>{gy}, w, TStoreAct{st}, Np, cv.ci, K, K);
+      return tc_gemm(net, GatherIm2col<1>{gy}, w, TStoreAct{st}, Np, cv.ci, K, K);
+    }
     flip_kernel<<<grid1((long long)cv.co * cv.ci * kk), 256, 0, net->stream>>>(
         net->pb + cv.w_off, net->pt + cv.w_off, cv.co, cv.ci, cv.ks);
     LoadW la{net->pt + cv.w_off, cv.co * kk};
     LoadIm2col lb{gy, cv.ks};
-    StoreAct st{net->gact[gx_id], net->act_c[gx_id], gx_coff, cv.H, cv.W, nullptr, 0, 1};
     dim3 grid((Np + BN - 1) / BN, (cv.ci + BM - 1) / BM, 1);
     gemm_kernel<<<grid, GT, 0, net->stream>>>(la, lb, st, cv.ci, Np, cv.co * kk, cv.co * kk);
   }
@@ -560,6 +804,11 @@ clbm_status nfail(clbm_net* n, clbm_status s, const std::string& m) {
   return s;
 }
 
+const char* const kTimeoutMsg =
+    "a tensor-core GEMM gave up waiting for its MMAs (results of this and later calls are invalid)";
+
+bool timed_out(const clbm_net* n) { return *(volatile int*)n->tflag != 0; }
+
 clbm_status cuda_status(clbm_net* n, cudaError_t e, const char* where) {
   if (e == cudaSuccess) return CLBM_OK;
   return nfail(n, CLBM_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
@@ -594,6 +843,9 @@ clbm_status clbm_net_destroy(clbm_net* n) {
   for (float* a : n->gact) cudaFree(a);
   cudaFree(n->part);
   cudaFree(n->loss_part);
+  if (n->tflag) cudaFreeHost(n->tflag);
+  cudaFree(n->packed);
+  cudaFree(n->d_pack);
   if (n->own_stream && n->stream) cudaStreamDestroy(n->stream);
   delete n;
   return CLBM_OK;
@@ -604,7 +856,8 @@ clbm_status clbm_net_create(const clbm_net_config* cfg, uint64_t seed, void* str
   *out = nullptr;
   const clbm_net_config& c = *cfg;
   if (c.levels < 2 || c.levels > kMaxLevels || c.base < 1 || c.in_ch < 1 || c.out_ch < 1 ||
-      c.max_batch < 1 || c.grid < 2 || (c.grid % (1 << (c.levels - 1))) != 0)
+      c.max_batch < 1 || c.grid < 2 || (c.grid % (1 << (c.levels - 1))) != 0 ||
+      (c.math != CLBM_NET_TENSOR && c.math != CLBM_NET_FP32))
     return CLBM_EINVAL;
   clbm_net* n = new (std::nothrow) clbm_net();
   if (!n) return CLBM_ENOMEM;
@@ -623,7 +876,7 @@ clbm_status clbm_net_create(const clbm_net_config* cfg, uint64_t seed, void* str
   const int L = c.levels, B = c.base, G = c.grid;
   long long off = 0;
   auto add_conv = [&](int ci, int co, int ks, int h) {
-    Conv cv{ci, co, ks, h, h, off, off + (long long)co * ci * ks * ks};
+    Conv cv{(int)n->convs.size(), ci, co, ks, h, h, off, off + (long long)co * ci * ks * ks};
     off = cv.b_off + co;
     n->convs.push_back(cv);
   };
@@ -657,6 +910,32 @@ clbm_status clbm_net_create(const clbm_net_config* cfg, uint64_t seed, void* str
   cudaMemset(n->v, 0, off * sizeof(float));
   cudaMemset(n->g, 0, off * sizeof(float));
   to_bf16_kernel<<<grid1(off), 256, 0, n->stream>>>(n->p, n->pb, off);
+  if (c.math == CLBM_NET_TENSOR) {
+    long long total = 0;
+    for (const Conv& cv : n->convs)
+      for (int tr = 0; tr < 2; ++tr) {
+        PackDesc d{};
+        d.w_off = cv.w_off;
+        d.dst_off = total;
+        d.co = cv.co;
+        d.ci = cv.ci;
+        d.kk = cv.ks * cv.ks;
+        d.transpose = tr;
+        d.N = tr ? cv.ci : cv.co;
+        d.K = (tr ? cv.co : cv.ci) * d.kk;
+        d.bn = tc::tile_n(d.N);
+        d.slices = (d.K + tc::kBK - 1) / tc::kBK;
+        d.size = (long long)((d.N + d.bn - 1) / d.bn) * d.slices * d.bn * tc::kBK;
+        total += (d.size + 63) / 64 * 64;  // keep every layer's tiles 128-byte aligned
+        n->packed_max = std::max(n->packed_max, d.size);
+        n->pack.push_back(d);
+      }
+    if (cudaMalloc(&n->packed, total * sizeof(__nv_bfloat16)) ||
+        cudaMalloc(&n->d_pack, n->pack.size() * sizeof(PackDesc)))
+      return bail(CLBM_ENOMEM);
+    cudaMemcpy(n->d_pack, n->pack.data(), n->pack.size() * sizeof(PackDesc), cudaMemcpyHostToDevice);
+    if (pack_weights(n) != cudaSuccess) return bail(CLBM_ECUDA);
+  }
   // activations
   n->plan = make_plan(n);
   for (size_t id = 0; id < n->act_c.size(); ++id) {
@@ -669,12 +948,20 @@ clbm_status clbm_net_create(const clbm_net_config* cfg, uint64_t seed, void* str
     n->act.push_back(a);
     n->gact.push_back(ga);
   }
+  // split-K partials: enough for the largest batch (fewer pixels never need more splits)
   long long cap = 0;
   for (const Conv& cv : n->convs) {
-    const long long splits = ((long long)c.max_batch * cv.H * cv.W + 4095) / 4096;
-    cap = std::max(cap, splits * cv.co * cv.ci * cv.ks * cv.ks);
+    const int Kd = cv.ci * cv.ks * cv.ks;
+    for (long long nb = 1; nb <= c.max_batch; ++nb) {
+      const long long Np = nb * cv.H * cv.W;
+      const long long kper = dw_kper(c.math == CLBM_NET_TENSOR, Np, Kd, cv.co);
+      cap = std::max(cap, ((Np + kper - 1) / kper) * cv.co * Kd);
+    }
   }
   n->part_cap = cap;
+  if (cudaHostAlloc(&n->tflag, sizeof(int), cudaHostAllocMapped) != cudaSuccess) return bail(CLBM_ENOMEM);
+  *n->tflag = 0;
+  if (cudaHostGetDevicePointer(&n->d_tflag, n->tflag, 0) != cudaSuccess) return bail(CLBM_ECUDA);
   if (cudaMalloc(&n->part, cap * sizeof(float)) || cudaMalloc(&n->loss_part, c.max_batch * sizeof(double)))
     return bail(CLBM_ENOMEM);
   if (cudaStreamSynchronize(n->stream) != cudaSuccess) return bail(CLBM_ECUDA);
@@ -702,6 +989,7 @@ clbm_status clbm_net_set_params(clbm_net* n, const float* src, int32_t on_device
                  on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice))
     return CLBM_ECUDA;
   to_bf16_kernel<<<grid1(n->nparam), 256, 0, n->stream>>>(n->p, n->pb, n->nparam);
+  if (pack_weights(n) != cudaSuccess) return nfail(n, CLBM_ECUDA, "pack weights");
   cudaMemsetAsync(n->m, 0, n->nparam * sizeof(float), n->stream);
   cudaMemsetAsync(n->v, 0, n->nparam * sizeof(float), n->stream);
   n->steps = 0;
@@ -710,6 +998,7 @@ clbm_status clbm_net_set_params(clbm_net* n, const float* src, int32_t on_device
 
 clbm_status clbm_net_forward(clbm_net* n, const float* x, int32_t N, float* y) {
   if (!n || !x || !y || N < 1 || N > n->cfg.max_batch) return CLBM_EINVAL;
+  if (timed_out(n)) return nfail(n, CLBM_ETIMEOUT, kTimeoutMsg);
   const Plan& P = n->plan;
   const long long in_e = (long long)N * n->cfg.in_ch * n->cfg.grid * n->cfg.grid;
   const long long out_e = (long long)N * n->cfg.out_ch * n->cfg.grid * n->cfg.grid;
@@ -749,6 +1038,7 @@ clbm_status clbm_net_gradients(clbm_net* n, const float* x, const float* target,
   if (!e) e = cudaMemcpyAsync(lp.data(), n->loss_part, N * sizeof(double), cudaMemcpyDeviceToHost, n->stream);
   if (!e) e = cudaStreamSynchronize(n->stream);
   if (e) return cuda_status(n, e, "gradients");
+  if (timed_out(n)) return nfail(n, CLBM_ETIMEOUT, kTimeoutMsg);
   double s = 0.0;
   for (double v : lp) s += v;
   if (loss) *loss = s / norm;
@@ -769,7 +1059,9 @@ clbm_status clbm_net_train_step(clbm_net* n, const float* x, const float* target
   const float c2 = 1.0f / (1.0f - std::pow(b2, (float)n->steps));
   adam_kernel<<<grid1(n->nparam), 256, 0, n->stream>>>(n->p, n->g, n->m, n->v, n->pb, n->nparam, lr,
                                                         b1, b2, 1e-8f, c1, c2);
-  return cuda_status(n, cudaGetLastError(), "adam");
+  cudaError_t e = cudaGetLastError();
+  if (!e) e = pack_weights(n);
+  return cuda_status(n, e, "adam");
 }
 
 }  // extern "C"

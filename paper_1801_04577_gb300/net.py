@@ -14,7 +14,11 @@ from . import clbm as _clbm
 
 class clbm_net_config(C.Structure):
     _fields_ = [("grid", C.c_int32), ("in_ch", C.c_int32), ("out_ch", C.c_int32),
-                ("base", C.c_int32), ("levels", C.c_int32), ("max_batch", C.c_int32)]
+                ("base", C.c_int32), ("levels", C.c_int32), ("max_batch", C.c_int32),
+                ("math", C.c_int32)]
+
+
+MATH = {"tensor": 0, "fp32": 1}  # CLBM_NET_TENSOR, CLBM_NET_FP32
 
 
 NET_EXPORTS = ["clbm_net_create", "clbm_net_param_count", "clbm_net_get_params",
@@ -70,8 +74,9 @@ class Net:
     """U-Net surrogate; see clbm_net_create for the architecture."""
 
     def __init__(self, grid: int, in_ch: int, out_ch: int, base: int, levels: int, max_batch: int,
-                 seed: int = 1, stream: Optional[int] = None):
-        self.cfg = clbm_net_config(grid, in_ch, out_ch, base, levels, max_batch)
+                 seed: int = 1, stream: Optional[int] = None, math: str = "tensor"):
+        self.math = math
+        self.cfg = clbm_net_config(grid, in_ch, out_ch, base, levels, max_batch, MATH[math])
         self.h = C.c_void_p()
         _check(load().clbm_net_create(C.byref(self.cfg), seed, stream, C.byref(self.h)), None,
                "clbm_net_create")

@@ -102,8 +102,9 @@ def generate(ws, tol: float = 1e-6, max_steps: int = 40000, check_every: int = 1
     return targets_from_fields(ws, fields), conv, el
 
 
-def make_net(G: int, base: int, levels: int, max_batch: int, seed: int = 7, stream=None) -> Net:
-    return Net(G, IN_CH, OUT_CH, base, levels, max_batch, seed=seed, stream=stream)
+def make_net(G: int, base: int, levels: int, max_batch: int, seed: int = 7, stream=None,
+             math: str = "tensor") -> Net:
+    return Net(G, IN_CH, OUT_CH, base, levels, max_batch, seed=seed, stream=stream, math=math)
 
 
 def train(net: Net, X, Y, M, epochs: int, batch: int, lr: float, seed: int = 11, log=None):

@@ -35,7 +35,8 @@ def test_net_create_rejects_bad_config():
     h = C.c_void_p()
     for cfg in [(30, 5, 3, 8, 3, 4),   # grid not divisible by 2^(levels-1)
                 (32, 5, 3, 8, 1, 4),   # too few levels
-                (32, 0, 3, 8, 3, 4)]:  # no input channels
+                (32, 0, 3, 8, 3, 4),   # no input channels
+                (32, 5, 3, 8, 3, 4, 7)]:  # unknown convolution arithmetic
         c = net.clbm_net_config(*cfg)
         assert L.clbm_net_create(C.byref(c), 1, None, C.byref(h)) == clbm.CLBM_EINVAL
 

@@ -1,6 +1,17 @@
 """Warm-start network: kernels against the FP64 reference, and the gain over
 rest starts.  The network, its backward pass and Adam run in the library's
-CUDA kernels; the reference is oracle/surrogate.py (float64, autograd)."""
+CUDA kernels; the reference is oracle/surrogate.py (float64, autograd).
+
+Tolerances.  FP32 CUDA-core convolutions: forward 1e-5, gradients 1e-4
+(max-norm relative), FP32 rounding only.  Tensor-core convolutions (both GEMM
+operands rounded to bfloat16): against the reference with the same roundings
+(rnd=bf16) the results are identical whenever every GEMM sum is exact in FP32
+(sparse dyadic weights: forward bit-exact, gradients to FP32 accumulation);
+with dense random weights the FP32-vs-FP64 difference of a sum flips an
+occasional bfloat16 rounding and the flips spread through the 19 layers, so
+the two agree only to the size of the bfloat16 noise itself: sqrt(2 x 19)
+roundings of 2^-8 relative give ~2.4e-2, bounded here by 2e-2 (forward, max
+relative to max |y|) and 5e-2 (per-layer gradients)."""
 import numpy as np
 import pytest
 
@@ -21,10 +32,22 @@ def _batch(G, cin, cout, N, seed):
     return x, t, m
 
 
+def _layer_errors(g, g_ref, shapes):
+    """max-norm relative error of every layer's weight and bias gradients"""
+    out, off = [], 0
+    for ci, co, k in shapes:
+        for n in (co * ci * k * k, co):
+            a, b = g[off:off + n], g_ref[off:off + n]
+            out.append(np.abs(a - b).max() / max(np.abs(b).max(), 1e-30))
+            off += n
+    return np.array(out)
+
+
 @pytest.mark.parametrize("G,base,levels,N", [(16, 4, 3, 2), (64, 24, 4, 2)])
 def test_net_forward_and_gradients_match_reference(G, base, levels, N):
+    """FP32 CUDA-core convolutions against the float64 reference."""
     from oracle import surrogate as S
-    net = Net(G, 5, 3, base, levels, N, seed=3)
+    net = Net(G, 5, 3, base, levels, N, seed=3, math="fp32")
     x, t, m = _batch(G, 5, 3, N, seed=G + base)
     xd, td, md = (torch.from_numpy(a).cuda() for a in (x, t, m))
     y = torch.empty((N, 3, G, G), dtype=torch.float32, device="cuda")
@@ -44,6 +67,73 @@ def test_net_forward_and_gradients_match_reference(G, base, levels, N):
             a, b = g[off:off + n], g_ref[off:off + n]
             assert np.abs(a - b).max() <= 1e-4 * max(np.abs(b).max(), 1e-12), (ci, co, k, n)
             off += n
+    net.close()
+
+
+def _sparse_dyadic_params(shapes, seed, nnz=4):
+    """Weights k/8 (k = +-1..4) on about nnz taps per output, biases j/16:
+    every GEMM sum of the network then holds few terms of short significands
+    and is exact in FP32 as well as in FP64."""
+    out = []
+    for li, (ci, co, k) in enumerate(shapes):
+        K = ci * k * k
+        r = I.splitmix64_uniform(seed + li, co * K * 2 + co)
+        keep = r[:co * K] < nnz / K
+        val = np.floor(r[co * K:2 * co * K] * 8) - 4
+        val[val >= 0] += 1
+        out.append(np.where(keep, val / 8.0, 0.0))
+        out.append(np.floor(r[2 * co * K:] * 8 - 4) / 16.0)
+    return np.concatenate(out).astype(np.float32)
+
+
+@pytest.mark.parametrize("G,base,levels,N", [(64, 24, 4, 2), (16, 48, 3, 2)])
+def test_tensor_core_net_exact_when_sums_are_exact(G, base, levels, N):
+    """tcgen05 path against the reference with bfloat16-rounded GEMM operands,
+    on a problem whose every sum is exact: the forward pass is bit-identical.
+    (64^2, widths 24..192: 1.1 M parameters, K up to 2592; widths 48..192:
+    input-gradient GEMMs with 288 columns in two tiles.)"""
+    from oracle import surrogate as S
+    cin, cout = 5, 4  # out_ch 4: the loss normalisation N G^2 4 is a power of two
+    shapes = layer_shapes(G, cin, cout, base, levels)
+    net = Net(G, cin, cout, base, levels, N, seed=3, math="tensor")
+    p = _sparse_dyadic_params(shapes, 100 + G + base)
+    net.set_params(p)
+    r = I.splitmix64_uniform(7, N * (cin + cout) * G * G)
+    x = (np.floor(r[:N * cin * G * G] * 9 - 4) / 4).reshape(N, cin, G, G).astype(np.float32)
+    t = (np.floor(r[N * cin * G * G:] * 9 - 4) / 4).reshape(N, cout, G, G).astype(np.float32)
+    xd, td = (torch.from_numpy(a).cuda() for a in (x, t))
+    y = torch.empty((N, cout, G, G), dtype=torch.float32, device="cuda")
+    net.forward(xd, y)
+    loss, g = net.gradients(xd, td, None)
+    assert (weights_as_used(net.get_params(), shapes) == p).all()
+    L_ref, g_ref, y_ref = S.loss_and_grad(p.astype(np.float64), shapes, levels, x, t, None, rnd=S.bf16)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(y.cpu().numpy(), y_ref.astype(np.float32))
+    assert loss == pytest.approx(L_ref, rel=1e-12)
+    e = _layer_errors(g, g_ref, shapes)
+    assert e.max() <= 5e-5, e
+    net.close()
+
+
+@pytest.mark.parametrize("G,base,levels,N", [(16, 4, 3, 2), (64, 24, 4, 2)])
+def test_tensor_core_net_matches_bf16_reference(G, base, levels, N):
+    """tcgen05 path with dense random weights against the reference with the
+    same bfloat16 roundings, within the bfloat16 noise (module docstring)."""
+    from oracle import surrogate as S
+    net = Net(G, 5, 3, base, levels, N, seed=3, math="tensor")
+    x, t, m = _batch(G, 5, 3, N, seed=G + base)
+    xd, td, md = (torch.from_numpy(a).cuda() for a in (x, t, m))
+    y = torch.empty((N, 3, G, G), dtype=torch.float32, device="cuda")
+    net.forward(xd, y)
+    loss, g = net.gradients(xd, td, md)
+    shapes = layer_shapes(G, 5, 3, base, levels)
+    p = weights_as_used(net.get_params(), shapes)
+    L_ref, g_ref, y_ref = S.loss_and_grad(p.astype(np.float64), shapes, levels, x, t, m, rnd=S.bf16)
+    torch.cuda.synchronize()
+    assert np.abs(y.cpu().numpy() - y_ref).max() <= 2e-2 * np.abs(y_ref).max()
+    assert loss == pytest.approx(L_ref, rel=1e-3)
+    e = _layer_errors(g, g_ref, shapes)
+    assert e.max() <= 5e-2, e
     net.close()
 
 

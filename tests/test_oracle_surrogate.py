@@ -70,3 +70,36 @@ def test_bf16_rounding_is_nearest_even():
     assert r[2] == np.float32(1.0078125)
     assert abs(r[3] - a[3]) <= 2.0 ** -7 * 4
     assert (r.view(np.uint32) & 0xFFFF == 0).all()
+
+
+def test_rounded_convolution_backward_matches_autograd_when_rounding_is_identity():
+    """The hand-written backward of the rounded convolution (input gradient by
+    conv2d_input, weight gradient by conv2d_weight, bias by a sum) reduces to
+    the finite-difference-pinned autograd network when nothing is rounded."""
+    shapes, params, x, t, mask, levels = _case(G=8, cin=3, cout=2, base=3, levels=3)
+    L0, g0, y0 = S.loss_and_grad(params, shapes, levels, x, t, mask)
+    L1, g1, y1 = S.loss_and_grad(params, shapes, levels, x, t, mask, rnd=lambda a: a)
+    assert L1 == pytest.approx(L0, rel=1e-13)
+    np.testing.assert_allclose(y1, y0, rtol=0, atol=1e-13)
+    np.testing.assert_allclose(g1, g0, rtol=0, atol=1e-12 * np.abs(g0).max())
+
+
+def test_oracle_bf16_rounding_values():
+    """bf16() rounds to float32 first, then to bfloat16 ties-to-even (spacing
+    2^-7 just above 1)."""
+    u = 2.0 ** -8
+    v = torch.tensor([1 + u, 1 + 3 * u, 1 + u + 2.0 ** -20, -(1 + 3 * u), 3.0, 1 + u + 2.0 ** -40],
+                     dtype=torch.float64)
+    want = [1.0, 1 + 4 * u, 1 + 2 * u, -(1 + 4 * u), 3.0, 1.0]
+    assert S.bf16(v).tolist() == want
+
+
+def test_bf16_network_differs_from_fp64_by_bf16_rounding_only():
+    """With rounding on, the loss moves by about the bf16 unit roundoff (2^-9
+    relative per operand), not by O(1): the rounding is applied to the GEMM
+    operands only."""
+    shapes, params, x, t, mask, levels = _case(G=8, cin=3, cout=2, base=3, levels=3)
+    L0, g0, y0 = S.loss_and_grad(params, shapes, levels, x, t, mask)
+    L1, g1, y1 = S.loss_and_grad(params, shapes, levels, x, t, mask, rnd=S.bf16)
+    assert 0 < abs(L1 - L0) / L0 < 2e-2
+    assert np.abs(y1 - y0).max() < 5e-2 * np.abs(y0).max()
