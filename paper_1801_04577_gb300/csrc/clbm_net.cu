@@ -134,9 +134,11 @@ __device__ __forceinline__ void put_chunk(uint8_t* dst, int r, int kc, const flo
                  tc::pack_bf16(v[6], v[7]));
 }
 
-// A(m = pixel, k = (channel, tap)) = x[channel] at pixel + tap offset (zero
-// outside the image): thread r gathers row r, so every load of a warp reads
-// 32 consecutive pixels.
+// A(m = pixel, k = tap * C + channel) = x[channel] at pixel + tap offset
+// (zero outside the image; tap-major K, the order of the packed weights).
+// Thread r gathers row r, so every load of a warp reads 32 consecutive
+// pixels.  With C a multiple of 8 every 16-byte chunk holds one tap and eight
+// channels: one offset and one bounds test per chunk.
 template <int KS>
 struct GatherIm2col {
   static constexpr bool kBulk = false;
@@ -145,7 +147,7 @@ struct GatherIm2col {
                                              int kend) const {
     constexpr int KK = KS * KS, R = KS / 2;
     const int r = threadIdx.x;
-    const int hw = x.H * x.W;
+    const int hw = x.H * x.W, C = x.C;
     const bool rv = r < rows_valid;
     int nb = 0, p = 0, yy = 0, xx = 0;
     if (rv) {
@@ -162,21 +164,35 @@ struct GatherIm2col {
       const int sy = yy + t / KS - R, sx = xx + t % KS - R;
       if (rv && sy >= 0 && sy < x.H && sx >= 0 && sx < x.W) vm |= 1u << t;
     }
-    int c = k0 / KK, t = k0 - c * KK;
+    if ((C & 7) == 0) {
+      int t = k0 / C, c = k0 - t * C;
 #pragma unroll
-    for (int kc = 0; kc < tc::kBK / 8; ++kc) {
-      float v[8];
+      for (int kc = 0; kc < tc::kBK / 8; ++kc) {
+        const bool ok = k0 + kc * 8 < kend && ((vm >> t) & 1u);
+        const float* s = src + c * hw + (t / KS - R) * x.W + (t % KS - R);
+        float v[8];
 #pragma unroll
-      for (int e = 0; e < 8; ++e) {
-        const int k = k0 + kc * 8 + e;
-        const int off = (t / KS - R) * x.W + (t % KS - R);
-        v[e] = (k < kend && ((vm >> t) & 1u)) ? __ldg(src + c * hw + off) : 0.0f;
-        if (++t == KK) {
-          t = 0;
-          ++c;
+        for (int e = 0; e < 8; ++e) v[e] = ok ? __ldg(s + e * hw) : 0.0f;
+        put_chunk(dst, r, kc, v);
+        c += 8;
+        if (c == C) {
+          c = 0;
+          ++t;
         }
       }
-      put_chunk(dst, r, kc, v);
+    } else {
+#pragma unroll 2
+      for (int kc = 0; kc < tc::kBK / 8; ++kc) {
+        float v[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          const int k = k0 + kc * 8 + e;
+          const int t = k / C, c = k - t * C;
+          const bool ok = k < kend && ((vm >> t) & 1u);
+          v[e] = ok ? __ldg(src + c * hw + (t / KS - R) * x.W + (t % KS - R)) : 0.0f;
+        }
+        put_chunk(dst, r, kc, v);
+      }
     }
   }
 };
@@ -262,8 +278,9 @@ struct TStorePartial {  // D(m = (ci, tap), n = co) of split z
 };
 
 // Pre-packed BF16 weights for the tensor-core GEMMs (tc::Packed layout), one
-// entry per layer and direction: forward B(n = co, k = (ci, tap)) = W, input
-// gradient B(n = ci, k = (co, tap')) = W with the taps flipped.
+// entry per layer and direction, K tap-major: forward B(n = co, k = tap * ci
+// + c) = W[co][c][tap], input gradient B(n = ci, k = tap' * co + o) =
+// W[o][ci][taps - 1 - tap'] (taps flipped).
 struct PackDesc {
   long long w_off;    // layer weights in the parameter vector
   long long dst_off;  // first element of this layer's packed buffer
@@ -287,11 +304,12 @@ __global__ void pack_weights_kernel(const PackDesc* __restrict__ descs, const __
     const int n = nt * d.bn + rg * 8 + r7, k = ks * tc::kBK + kc * 8 + e;
     __nv_bfloat16 v = __float2bfloat16_rn(0.0f);
     if (n < d.N && k < d.K) {
-      if (!d.transpose) {
-        v = w[d.w_off + (long long)n * d.K + k];
-      } else {  // n = ci, k = (co, t'): W[co][ci][kk - 1 - t']
-        const int co = k / d.kk, tp = k - co * d.kk;
-        v = w[d.w_off + ((long long)co * d.ci + n) * d.kk + (d.kk - 1 - tp)];
+      if (!d.transpose) {  // n = co, k = t * ci + c
+        const int t = k / d.ci, c = k - t * d.ci;
+        v = w[d.w_off + ((long long)n * d.ci + c) * d.kk + t];
+      } else {  // n = ci, k = t' * co + o
+        const int tp = k / d.co, o = k - tp * d.co;
+        v = w[d.w_off + ((long long)o * d.ci + n) * d.kk + (d.kk - 1 - tp)];
       }
     }
     out[d.dst_off + i] = v;
@@ -368,23 +386,30 @@ __global__ void sum_splits_kernel(const float* __restrict__ part, int splits, lo
   }
 }
 
-// db[c] = sum over samples and pixels of g[n][c][p] (one block per channel, fixed order)
-__global__ void bias_grad_kernel(Act g, int N, float* __restrict__ db) {
+// Bias gradient db[c] = sum over samples and pixels of g[n][c][p], in two
+// deterministic stages: block (s, c) sums chunk s of channel c's values
+// (sample-major) into part[s][c]; sum_splits_kernel then adds the chunks in
+// order.
+constexpr int kBiasChunk = 4096;
+
+__global__ void bias_partial_kernel(Act g, int N, float* __restrict__ part) {
   __shared__ float sh[GT];
-  const int c = blockIdx.x;
+  const int s = blockIdx.x, c = blockIdx.y;
   const int hw = g.H * g.W;
-  float s = 0.0f;
-  for (long long k = threadIdx.x; k < (long long)N * hw; k += blockDim.x) {
+  const long long tot = (long long)N * hw;
+  const long long k0 = (long long)s * kBiasChunk, k1 = min(tot, k0 + kBiasChunk);
+  float acc = 0.0f;
+  for (long long k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
     const int nb = (int)(k / hw), p = (int)(k - (long long)nb * hw);
-    s += g.base[((long long)nb * g.cs + g.coff + c) * hw + p];
+    acc += g.base[((long long)nb * g.cs + g.coff + c) * hw + p];
   }
-  sh[threadIdx.x] = s;
+  sh[threadIdx.x] = acc;
   __syncthreads();
   for (int o = GT / 2; o > 0; o >>= 1) {
     if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
     __syncthreads();
   }
-  if (threadIdx.x == 0) db[c] = sh[0];
+  if (threadIdx.x == 0) part[(long long)s * gridDim.y + c] = sh[0];
 }
 
 // g *= (y > 0) over one activation view (ReLU backward, in place on g)
@@ -677,7 +702,11 @@ cudaError_t conv_backward(clbm_net* net, const Conv& cv, Act x, Act gy, int gx_i
     }
     const long long n = (long long)cv.co * Kd;
     sum_splits_kernel<<<grid1(n), 256, 0, net->stream>>>(net->part, splits, n, net->g + cv.w_off);
-    bias_grad_kernel<<<cv.co, GT, 0, net->stream>>>(gy, N, net->g + cv.b_off);
+    // bias: the split-K partials are consumed, so part holds the chunk sums next
+    const int chunks = (Np + kBiasChunk - 1) / kBiasChunk;
+    if ((long long)chunks * cv.co > net->part_cap) return cudaErrorInvalidValue;
+    bias_partial_kernel<<<dim3(chunks, cv.co), GT, 0, net->stream>>>(gy, N, net->part);
+    sum_splits_kernel<<<grid1(cv.co), 256, 0, net->stream>>>(net->part, chunks, cv.co, net->g + cv.b_off);
   }
   if (gx_id >= 0) {  // input gradient: M = ci, N = pixels, K = co*t, with flipped weights
     const int kk = cv.ks * cv.ks;
@@ -956,6 +985,7 @@ clbm_status clbm_net_create(const clbm_net_config* cfg, uint64_t seed, void* str
       const long long Np = nb * cv.H * cv.W;
       const long long kper = dw_kper(c.math == CLBM_NET_TENSOR, Np, Kd, cv.co);
       cap = std::max(cap, ((Np + kper - 1) / kper) * cv.co * Kd);
+      cap = std::max(cap, ((Np + kBiasChunk - 1) / kBiasChunk) * cv.co);  // bias chunk sums
     }
   }
   n->part_cap = cap;
