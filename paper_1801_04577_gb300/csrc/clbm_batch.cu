@@ -80,17 +80,20 @@ __global__ void batch_scan_kernel(int n, const int* __restrict__ active,
   ctl->n_active = nact;
 }
 
+// Tiles {lattice, row, first x, 0} of rows y0 .. y0 + rows - 1 (the rows that
+// are not boundary rows) of every active lattice.
 __global__ void batch_tiles_kernel(int n, const int* __restrict__ active,
                                    const long long* __restrict__ offset,
-                                   const int* __restrict__ group_of, const int* __restrict__ ny_of,
+                                   const int* __restrict__ group_of, const int* __restrict__ rows_of,
                                    const int* __restrict__ tpr_of, const int* __restrict__ width_of,
-                                   int4* const* __restrict__ group_tiles) {
+                                   const int* __restrict__ y0_of, int4* const* __restrict__ group_tiles) {
   const int i = blockIdx.x;
   if (i >= n || !active[i]) return;
   int4* dst = group_tiles[group_of[i]] + offset[i];
-  const int tpr = tpr_of[i], w = width_of[i];
-  const int total = ny_of[i] * tpr;
-  for (int k = threadIdx.x; k < total; k += blockDim.x) dst[k] = make_int4(i, k / tpr, (k % tpr) * w, 0);
+  const int tpr = tpr_of[i], w = width_of[i], y0 = y0_of[i];
+  const int total = rows_of[i] * tpr;
+  for (int k = threadIdx.x; k < total; k += blockDim.x)
+    dst[k] = make_int4(i, y0 + k / tpr, (k % tpr) * w, 0);
 }
 
 }  // namespace
@@ -103,9 +106,10 @@ struct clbm_batch {
   bool own_stream = false;
   void* arena[2] = {nullptr, nullptr};
   std::vector<clbm_ctx*> views;
-  std::vector<int> nx, ny, masked, width, group;
+  std::vector<int> nx, ny, py, masked, width, group;
   std::vector<long long> nodes;
   std::vector<int> grid;  // per group
+  std::vector<long long> group_base = std::vector<long long>(kBatchGroups, 0);  // tile-list offsets
   BatchLat* d_lats = nullptr;
   int* d_active = nullptr;
   double* d_res = nullptr;
@@ -113,7 +117,7 @@ struct clbm_batch {
   BatchCtl* d_ctl = nullptr;
   BatchCtl* h_ctl = nullptr;  // pinned
   long long* d_offset = nullptr;
-  int* d_ints = nullptr;  // group_of, tiles_of, ny_of, tpr_of, width_of (5 x n)
+  int* d_ints = nullptr;  // group_of, tiles_of, rows_of, tpr_of, width_of, y0_of (6 x n)
   int4* d_tiles = nullptr;
   long long tile_cap = 0;
   int4** d_group_tiles = nullptr;
@@ -121,6 +125,8 @@ struct clbm_batch {
   int* d_snap_valid = nullptr;
   int2* d_bent = nullptr;  // boundary entries {lattice, node} of all lattices
   int nbent = 0;
+  double* d_rpart = nullptr;  // residual chunk sums
+  int res_chunks = 1;
   cudaGraphExec_t exec = nullptr;
   int exec_K = 0;
   double exec_tol = -1.0;
@@ -138,25 +144,34 @@ static clbm_status bfail(clbm_batch* b, clbm_status s, const std::string& m) {
     if (e_ != cudaSuccess) return bfail((b), CLBM_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
   } while (0)
 
+// Rows that get interior tiles: all rows of a periodic y axis, else all but the
+// first and last (boundary rows).
+static int interior_rows(const clbm_batch* b, int i) {
+  return b->py[i] ? b->ny[i] : std::max(b->ny[i] - 2, 0);
+}
+
 // Upload the per-lattice launch layout (group, tile counts) for the current widths.
 static clbm_status upload_layout(clbm_batch* b, const std::vector<int>& active) {
   const int n = b->n;
-  std::vector<int> ints(5 * (size_t)n);
+  std::vector<int> ints(6 * (size_t)n);
   std::vector<long long> gcap(kBatchGroups, 0);
   for (int i = 0; i < n; ++i) {
     const int w = 32 * b->width[i];
     const int tpr = (b->nx[i] + w - 1) / w;
+    const int rows = interior_rows(b, i);
     b->group[i] = group_id(b->width[i]);
     ints[i] = b->group[i];
-    ints[n + i] = b->ny[i] * tpr;
-    ints[2 * n + i] = b->ny[i];
+    ints[n + i] = rows * tpr;
+    ints[2 * n + i] = rows;
     ints[3 * n + i] = tpr;
     ints[4 * n + i] = w;
-    gcap[b->group[i]] += (long long)b->ny[i] * tpr;
+    ints[5 * n + i] = b->py[i] ? 0 : 1;
+    gcap[b->group[i]] += (long long)rows * tpr;
   }
   std::vector<int4*> bases(kBatchGroups);
   long long off = 0;
   for (int g = 0; g < kBatchGroups; ++g) {
+    b->group_base[g] = off;
     bases[g] = b->d_tiles + off;
     off += gcap[g];
   }
@@ -174,24 +189,18 @@ static clbm_status build_tiles(clbm_batch* b) {
   batch_scan_kernel<<<1, 32, 0, b->stream>>>(n, b->d_active, gi, gi + n, b->d_offset, b->d_ctl);
   BCUDA(b, cudaGetLastError());
   batch_tiles_kernel<<<n, 256, 0, b->stream>>>(n, b->d_active, b->d_offset, gi, gi + 2 * n, gi + 3 * n,
-                                               gi + 4 * n, b->d_group_tiles);
+                                               gi + 4 * n, gi + 5 * n, b->d_group_tiles);
   BCUDA(b, cudaGetLastError());
   return CLBM_OK;
 }
 
 // One step of every active lattice; parity = which buffer holds the current state.
-// Interior tiles first (one launch per tile-width group), then the boundary nodes.
+// Interior tiles first (one launch per tile-width group), then the boundary nodes
+// (which, next to solids, replace the provisional values the tiles wrote).
 static clbm_status launch_steps(clbm_batch* b, int parity, int tstep) {
   std::vector<int> used(kBatchGroups, 0);
-  std::vector<long long> base(kBatchGroups, 0);
   for (int i = 0; i < b->n; ++i) used[b->group[i]] = 1;
-  long long off = 0;
-  for (int g = 0; g < kBatchGroups; ++g) {  // group bases, as in upload_layout
-    base[g] = off;
-    for (int i = 0; i < b->n; ++i)
-      if (b->group[i] == g)
-        off += (long long)b->ny[i] * ((b->nx[i] + 32 * b->width[i] - 1) / (32 * b->width[i]));
-  }
+  const std::vector<long long>& base = b->group_base;  // as in upload_layout
   for (int g = 0; g < kBatchGroups; ++g) {
     if (!used[g]) continue;
     const int v = kWidthChoices[g];
@@ -221,6 +230,7 @@ static void release(clbm_batch* b) {
   cudaFree(b->d_tiles);
   cudaFree(b->d_group_tiles);
   cudaFree(b->d_bent);
+  cudaFree(b->d_rpart);
   cudaFree(b->d_snap);
   cudaFree(b->d_snap_valid);
   if (b->h_ctl) cudaFreeHost(b->h_ctl);
@@ -348,6 +358,7 @@ clbm_status clbm_batch_create(const clbm_batch_item* items, int32_t n, int32_t a
     if (st != CLBM_OK) return bail(st);
     b->nx.push_back(it.params.nx);
     b->ny.push_back(it.params.ny);
+    b->py.push_back(it.params.periodic_y ? 1 : 0);
     b->nodes.push_back((long long)it.params.nx * it.params.ny);
     cap += (long long)it.params.ny * ((it.params.nx + 31) / 32);
   }
@@ -392,10 +403,17 @@ clbm_status clbm_batch_create(const clbm_batch_item* items, int32_t n, int32_t a
       cudaMalloc(&b->d_conv, n * sizeof(long long)) != cudaSuccess ||
       cudaMalloc(&b->d_ctl, sizeof(BatchCtl)) != cudaSuccess ||
       cudaMalloc(&b->d_offset, n * sizeof(long long)) != cudaSuccess ||
-      cudaMalloc(&b->d_ints, 5 * (size_t)n * sizeof(int)) != cudaSuccess ||
+      cudaMalloc(&b->d_ints, 6 * (size_t)n * sizeof(int)) != cudaSuccess ||
       cudaMalloc(&b->d_tiles, std::max<long long>(cap, 1) * sizeof(int4)) != cudaSuccess ||
       cudaMalloc(&b->d_group_tiles, kBatchGroups * sizeof(int4*)) != cudaSuccess ||
       cudaMallocHost(&b->h_ctl, sizeof(BatchCtl)) != cudaSuccess) {
+    cudaGetLastError();
+    return bail(CLBM_ENOMEM);
+  }
+  long long maxnodes = 1;
+  for (int i = 0; i < n; ++i) maxnodes = std::max(maxnodes, b->nodes[i]);
+  b->res_chunks = (int)((maxnodes + L->residual_chunk - 1) / L->residual_chunk);
+  if (cudaMalloc(&b->d_rpart, (size_t)n * b->res_chunks * 8 * sizeof(double)) != cudaSuccess) {
     cudaGetLastError();
     return bail(CLBM_ENOMEM);
   }
@@ -463,14 +481,14 @@ clbm_status clbm_batch_solve(clbm_batch* b, double tol, int64_t max_steps, int32
     clbm_status cst = CLBM_OK;
     for (int j = 0; j < K && cst == CLBM_OK; ++j) cst = launch_steps(b, j & 1, j);
     if (cst == CLBM_OK && b->L->batch_residual(b->d_lats, b->d_active, b->d_snap_valid, b->d_res, n, K,
-                                               b->stream) != cudaSuccess)
+                                               b->d_rpart, b->res_chunks, b->stream) != cudaSuccess)
       cst = CLBM_ECUDA;
     if (cst == CLBM_OK) {
       batch_update_kernel<<<1, 256, 0, b->stream>>>(n, b->d_active, b->d_res, tol, b->d_conv, b->d_ctl, K);
       const int* gi = b->d_ints;
       batch_scan_kernel<<<1, 32, 0, b->stream>>>(n, b->d_active, gi, gi + n, b->d_offset, b->d_ctl);
       batch_tiles_kernel<<<n, 256, 0, b->stream>>>(n, b->d_active, b->d_offset, gi, gi + 2 * n,
-                                                   gi + 3 * n, gi + 4 * n, b->d_group_tiles);
+                                                   gi + 3 * n, gi + 4 * n, gi + 5 * n, b->d_group_tiles);
       if (cudaGetLastError() != cudaSuccess) cst = CLBM_ECUDA;
       if (cst == CLBM_OK &&
           cudaMemcpyAsync(b->h_ctl, b->d_ctl, sizeof(BatchCtl), cudaMemcpyDeviceToHost, b->stream) != cudaSuccess)

@@ -100,7 +100,8 @@ struct Launchers {
   cudaError_t (*nusselt)(const DevGeom& g, const DevCoef& c, const void* buf, const NuLink* links,
                          int nlinks, double* partials, int nblocks, cudaStream_t s);
   size_t elem_bytes;
-  // batched interior step over a tile list (tile = {lattice, row, first x, 0}); V = nodes per lane
+  // batched interior step over a tile list (tile = {lattice, row, first x, 0}; tiles skip the
+  // first and last column); V = nodes per lane
   cudaError_t (*batch_step)(int V, const BatchLat* lats, const int4* tiles, const int* count,
                             int parity, const long long* t, int tstep, int stochastic, int grid,
                             cudaStream_t s);
@@ -114,9 +115,12 @@ struct Launchers {
   cudaError_t (*average)(void* a, const void* b, long long n, cudaStream_t s);
 
   // per-lattice residual: change of (T, ux, uy) since the previous check (snapshot), per step
-  // (divided by K); 1e300 when there is no snapshot yet, +inf if a value is non-finite
+  // (divided by K); 1e300 when there is no snapshot yet, +inf if a value is non-finite.
+  // part: n * maxchunks * 8 doubles of scratch, maxchunks >= chunks of the largest lattice
   cudaError_t (*batch_residual)(const BatchLat* lats, const int* active, int* snap_valid,
-                                double* res, int n, int K, cudaStream_t s);
+                                double* res, int n, int K, double* part, int maxchunks,
+                                cudaStream_t s);
+  int residual_chunk;  // nodes per residual chunk
 };
 
 extern const Launchers kLaunchF64;

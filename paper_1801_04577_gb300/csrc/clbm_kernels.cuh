@@ -776,6 +776,28 @@ __device__ __forceinline__ void node_macros(const DevCoef& c, const S* __restric
   uy = (jy - 0.5 * Fy) / rho;
 }
 
+// The same in the collision's arithmetic R (FP32 below FP64 storage).
+template <typename S, typename R>
+__device__ __forceinline__ void node_macros_r(const DevCoef& c, const S* __restrict__ b,
+                                              long long plane, long long i, R& rho, R& ux, R& uy,
+                                              R& T) {
+  R f[9], s = R(0);
+#pragma unroll
+  for (int q = 0; q < 9; ++q) f[q] = (R)to_r(b[q * plane + i]);
+#pragma unroll
+  for (int q = 9; q < 14; ++q) s += (R)to_r(b[q * plane + i]);
+  const R qv = c.vh ? (R)to_r(b[14 * plane + i]) : R(0);
+  T = (R)c.T0 + s - R(0.5) * ((R)c.Q + qv);
+  const R Fx = (R)c.Fvx, Fy = (R)c.Fvy + (R)(c.rho0 * c.gbeta) * (T - R(0.5) * qv - (R)c.T0);
+  const R dr = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
+  rho = (R)c.rho0 + dr;
+  const R jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
+  const R jy = (f[2] - f[4]) + (f[5] - f[7]) + (f[6] - f[8]);
+  const R inv = R(1) / rho;
+  ux = (jx - R(0.5) * Fx) * inv;
+  uy = (jy - R(0.5) * Fy) * inv;
+}
+
 template <typename S>
 __global__ void moments_kernel(const DevGeom g, const DevCoef c, const S* __restrict__ b,
                                double* __restrict__ rho, double* __restrict__ ux,
@@ -877,6 +899,8 @@ __global__ void __launch_bounds__(kRedThreads)
 // lattice, row, x), so it stays on one lattice for many tiles; the lattice's
 // descriptor is copied into a per-warp shared-memory slot when it changes and
 // read from there, instead of chasing it through global memory on every tile.
+// Tiles cover only the rows that are not boundary rows and skip the first and
+// last column: those nodes belong to the boundary launch that follows.
 template <typename S, int V, bool VH>
 __global__ void __launch_bounds__(kStepThreads, 4)
     batch_step_kernel(const BatchLat* __restrict__ lats, const int4* __restrict__ tiles,
@@ -911,9 +935,9 @@ __global__ void __launch_bounds__(kStepThreads, 4)
       cur = tl.x;
       c = make_co<R>(L.c);
     }
-    step_tile<S, V, false, VH>(L.g, c, static_cast<const S*>(L.buf[parity]),
-                               static_cast<S*>(L.buf[parity ^ 1]), tl.y, tl.z, lane, seed,
-                               stochastic);
+    step_tile<S, V, true, VH>(L.g, c, static_cast<const S*>(L.buf[parity]),
+                              static_cast<S*>(L.buf[parity ^ 1]), tl.y, tl.z, lane, seed,
+                              stochastic);
   }
 }
 
@@ -943,59 +967,85 @@ __global__ void __launch_bounds__(kRedThreads)
   }
 }
 
-// Convergence measure of every active lattice, one block per lattice, FP64 in
-// a fixed order: max over (T, ux, uy) of ||phi(t) - phi(t - K)||_2 /
-// (K ||phi(t)||_2), against the snapshot taken at the previous check, which is
-// then replaced.  Comparing states K (even) steps apart is blind to the
-// period-2 oscillation a closed cavity can keep at a small amplitude, which
-// would otherwise hold a one-step residual above the tolerance.
+// Convergence measure of every active lattice in FP64: max over (T, ux, uy) of
+// ||phi(t) - phi(t - K)||_2 / (K ||phi(t)||_2), against the snapshot taken at
+// the previous check, which is then replaced.  Comparing states K (even) steps
+// apart is blind to the period-2 oscillation a closed cavity can keep at a
+// small amplitude, which would otherwise hold a one-step residual above the
+// tolerance.  Two deterministic stages: block (i, ch) sums chunk ch
+// (kResChunk nodes) of lattice i into part[i][ch][0..7]; one thread per
+// lattice then adds its chunks in order.
+constexpr int kResChunk = 8192;
+
 template <typename S>
 __global__ void __launch_bounds__(kRedThreads)
-    batch_residual_kernel(const BatchLat* __restrict__ lats, const int* __restrict__ active,
-                          int* __restrict__ snap_valid, double* __restrict__ res, int K) {
-  const int i = blockIdx.x;
+    batch_residual_partial_kernel(const BatchLat* __restrict__ lats, const int* __restrict__ active,
+                                  double* __restrict__ part, int maxchunks) {
+  const int i = blockIdx.x, ch = blockIdx.y;
   if (!active[i]) return;
   const BatchLat* L = lats + i;
   const DevGeom& g = L->g;
-  const S* cur = static_cast<const S*>(L->buf[0]);
   const long long n = (long long)g.ny * g.nx;
+  const long long k0 = (long long)ch * kResChunk;
+  if (k0 >= n) return;
+  const long long k1 = k0 + kResChunk < n ? k0 + kResChunk : n;
+  const S* cur = static_cast<const S*>(L->buf[0]);
   double* snap = L->snap;
-  const bool have = snap_valid[i] != 0;
-  double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-  for (long long k = threadIdx.x; k < n; k += blockDim.x) {
+  // per-node values and per-thread sums (at most kResChunk / blockDim nodes)
+  // in the collision's arithmetic (FP32 below FP64 storage, where FP64 is
+  // slow); block sums in FP64
+  using R = typename Traits<S>::R;
+  R a[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  for (long long k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
     const int y = (int)(k / g.nx), x = (int)(k - (long long)y * g.nx);
     const long long idx = (long long)y * g.pitch + x;
     if (g.flags && (g.flags[idx] & kFlagSolid)) continue;
-    double r1, u1, v1, t1;
-    node_macros(L->c, cur, g.plane, idx, r1, u1, v1, t1);
-    const double t0 = snap[k], u0 = snap[n + k], v0 = snap[2 * n + k];
-    acc[0] += (t1 - t0) * (t1 - t0);
-    acc[1] += t1 * t1;
-    acc[2] += (u1 - u0) * (u1 - u0);
-    acc[3] += u1 * u1;
-    acc[4] += (v1 - v0) * (v1 - v0);
-    acc[5] += v1 * v1;
-    if (!isfinite(r1) || !isfinite(u1) || !isfinite(v1) || !isfinite(t1)) acc[6] += 1.0;
+    R r1, u1, v1, t1;
+    node_macros_r(L->c, cur, g.plane, idx, r1, u1, v1, t1);
+    const R t0 = (R)snap[k], u0 = (R)snap[n + k], v0 = (R)snap[2 * n + k];
+    a[0] += (t1 - t0) * (t1 - t0);
+    a[1] += t1 * t1;
+    a[2] += (u1 - u0) * (u1 - u0);
+    a[3] += u1 * u1;
+    a[4] += (v1 - v0) * (v1 - v0);
+    a[5] += v1 * v1;
+    if (!isfinite(r1) || !isfinite(u1) || !isfinite(v1) || !isfinite(t1)) a[6] += R(1);
     snap[k] = t1;
     snap[n + k] = u1;
     snap[2 * n + k] = v1;
   }
+  double acc[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) acc[q] = (double)a[q];
   __shared__ double tot[8];
   block_sum_store<8>(acc, tot);
   __syncthreads();
-  if (threadIdx.x == 0) {
-    double best = 0.0;
-    for (int q = 0; q < 3; ++q) {
-      const double den = sqrt(tot[2 * q + 1]) > 1e-30 ? sqrt(tot[2 * q + 1]) : 1e-30;
-      const double v = sqrt(tot[2 * q]) / den;
-      best = v > best ? v : best;
-    }
-    best /= (double)K;
-    if (!have) best = 1e300;
-    if (tot[6] != 0.0 || !isfinite(best)) best = INFINITY;
-    res[i] = best;
-    snap_valid[i] = 1;
+  if (threadIdx.x < 8) part[((long long)i * maxchunks + ch) * 8 + threadIdx.x] = tot[threadIdx.x];
+}
+
+template <typename S>
+__global__ void batch_residual_final_kernel(const BatchLat* __restrict__ lats, const int* __restrict__ active,
+                                            int* __restrict__ snap_valid, const double* __restrict__ part,
+                                            int maxchunks, double* __restrict__ res, int n, int K) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n || !active[i]) return;
+  const DevGeom& g = lats[i].g;
+  const long long nodes = (long long)g.ny * g.nx;
+  const int nch = (int)((nodes + kResChunk - 1) / kResChunk);
+  double tot[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  for (int ch = 0; ch < nch; ++ch)
+    for (int q = 0; q < 8; ++q) tot[q] += part[((long long)i * maxchunks + ch) * 8 + q];
+  double best = 0.0;
+  for (int q = 0; q < 3; ++q) {
+    const double den = sqrt(tot[2 * q + 1]) > 1e-30 ? sqrt(tot[2 * q + 1]) : 1e-30;
+    const double v = sqrt(tot[2 * q]) / den;
+    best = v > best ? v : best;
   }
+  best /= (double)K;
+  if (!snap_valid[i]) best = 1e300;
+  if (tot[6] != 0.0 || !isfinite(best)) best = INFINITY;
+  res[i] = best;
+  snap_valid[i] = 1;
 }
 
 // a <- (a + b) / 2 over every stored value (both post-collision states of a
@@ -1138,8 +1188,12 @@ struct LaunchImpl {
   }
 
   static cudaError_t batch_residual(const BatchLat* lats, const int* active, int* snap_valid,
-                                    double* res, int n, int K, cudaStream_t s) {
-    batch_residual_kernel<S><<<n, kRedThreads, 0, s>>>(lats, active, snap_valid, res, K);
+                                    double* res, int n, int K, double* part, int maxchunks,
+                                    cudaStream_t s) {
+    batch_residual_partial_kernel<S><<<dim3(n, maxchunks), kRedThreads, 0, s>>>(lats, active, part,
+                                                                                maxchunks);
+    batch_residual_final_kernel<S><<<(n + 255) / 256, 256, 0, s>>>(lats, active, snap_valid, part,
+                                                                 maxchunks, res, n, K);
     return cudaGetLastError();
   }
 
@@ -1156,6 +1210,7 @@ struct LaunchImpl {
     L.batch_boundary = &batch_boundary;
     L.batch_grid = &batch_grid;
     L.batch_residual = &batch_residual;
+    L.residual_chunk = kResChunk;
     L.vec = V;
     L.step = &step;
     L.init = &init;
