@@ -139,6 +139,7 @@ static DevCoef make_coef(const clbm_ctx* c) {
   k.cT2 = c->p.cT2;
   k.vh = c->p.viscous_heating ? 1 : 0;
   k.pad = 0;
+  fill_f32(k);
   return k;
 }
 

@@ -36,12 +36,45 @@ struct DevGeom {
 
 // Relaxation and forcing constants in FP64 (converted to the compute type
 // inside the kernels).  s3 and lambda2 are already resolved.
+// The same constants rounded once to FP32 on the host, for the kernels that
+// compute in FP32 (GB300's FP64 rate is a small fraction of its FP32 rate, so
+// converting them per thread is not free).
+struct CoefF32 {
+  float rho0, T0, s_nu, s_b, s3, s4, l1, l2;
+  float rgb;  // rho0 * g beta
+  float Fvx, Fvy, Q, hQ, cT2;
+  float vhc;  // viscous source: 3 s_nu^2 (1/s_nu - 1/2), 0 when off
+  float pad;
+};
+
 struct DevCoef {
   double s_nu, s_b, s3, s4, l0, l1, l2;
   double rho0, T0, gbeta, Fvx, Fvy, Q, cT2;
   int vh;  // 1: viscous dissipation source (stored as a 15th plane, Q_v at each node)
   int pad;
+  CoefF32 f;  // filled by fill_f32
 };
+
+// FP32 copies of a DevCoef's constants (each computed in FP64, then rounded).
+inline void fill_f32(DevCoef& k) {
+  CoefF32& o = k.f;
+  o.rho0 = (float)k.rho0;
+  o.T0 = (float)k.T0;
+  o.s_nu = (float)k.s_nu;
+  o.s_b = (float)k.s_b;
+  o.s3 = (float)k.s3;
+  o.s4 = (float)k.s4;
+  o.l1 = (float)k.l1;
+  o.l2 = (float)k.l2;
+  o.rgb = (float)(k.rho0 * k.gbeta);
+  o.Fvx = (float)k.Fvx;
+  o.Fvy = (float)k.Fvy;
+  o.Q = (float)k.Q;
+  o.hQ = (float)(0.5 * k.Q);
+  o.cT2 = (float)k.cT2;
+  o.vhc = (float)(k.vh ? 3.0 * k.s_nu * k.s_nu * (1.0 / k.s_nu - 0.5) : 0.0);
+  o.pad = 0.0f;
+}
 
 struct StepArgs {
   DevGeom g;

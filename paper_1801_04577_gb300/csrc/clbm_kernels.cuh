@@ -36,6 +36,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "clbm_internal.h"
 
 namespace clbm {
@@ -215,22 +217,41 @@ struct Co {
 template <typename R>
 __host__ __device__ __forceinline__ Co<R> make_co(const DevCoef& c) {
   Co<R> o;
-  o.rho0 = (R)c.rho0;
-  o.T0 = (R)c.T0;
-  o.s_nu = (R)c.s_nu;
-  o.s_b = (R)c.s_b;
-  o.s3 = (R)c.s3;
-  o.s4 = (R)c.s4;
-  o.l1 = (R)c.l1;
-  o.l2 = (R)c.l2;
-  o.rgb = (R)(c.rho0 * c.gbeta);
-  o.Fvx = (R)c.Fvx;
-  o.Fvy = (R)c.Fvy;
-  o.Q = (R)c.Q;
-  o.hQ = (R)(0.5 * c.Q);
-  o.cT2 = (R)c.cT2;
-  // nu (D^2 + G^2) with G = -3 s_nu k~11/rho, D = -3 s_nu (k~20 - k~02)/(2 rho), nu = (1/s_nu - 1/2)/3
-  o.vhc = (R)(c.vh ? 3.0 * c.s_nu * c.s_nu * (1.0 / c.s_nu - 0.5) : 0.0);
+  if constexpr (std::is_same<R, float>::value) {  // rounded on the host
+    const CoefF32& f = c.f;
+    o.rho0 = f.rho0;
+    o.T0 = f.T0;
+    o.s_nu = f.s_nu;
+    o.s_b = f.s_b;
+    o.s3 = f.s3;
+    o.s4 = f.s4;
+    o.l1 = f.l1;
+    o.l2 = f.l2;
+    o.rgb = f.rgb;
+    o.Fvx = f.Fvx;
+    o.Fvy = f.Fvy;
+    o.Q = f.Q;
+    o.hQ = f.hQ;
+    o.cT2 = f.cT2;
+    o.vhc = f.vhc;
+  } else {
+    o.rho0 = (R)c.rho0;
+    o.T0 = (R)c.T0;
+    o.s_nu = (R)c.s_nu;
+    o.s_b = (R)c.s_b;
+    o.s3 = (R)c.s3;
+    o.s4 = (R)c.s4;
+    o.l1 = (R)c.l1;
+    o.l2 = (R)c.l2;
+    o.rgb = (R)(c.rho0 * c.gbeta);
+    o.Fvx = (R)c.Fvx;
+    o.Fvy = (R)c.Fvy;
+    o.Q = (R)c.Q;
+    o.hQ = (R)(0.5 * c.Q);
+    o.cT2 = (R)c.cT2;
+    // nu (D^2 + G^2) with G = -3 s_nu k~11/rho, D = -3 s_nu (k~20 - k~02)/(2 rho), nu = (1/s_nu - 1/2)/3
+    o.vhc = (R)(c.vh ? 3.0 * c.s_nu * c.s_nu * (1.0 / c.s_nu - 0.5) : 0.0);
+  }
   return o;
 }
 
@@ -778,7 +799,7 @@ __device__ __forceinline__ void node_macros(const DevCoef& c, const S* __restric
 
 // The same in the collision's arithmetic R (FP32 below FP64 storage).
 template <typename S, typename R>
-__device__ __forceinline__ void node_macros_r(const DevCoef& c, const S* __restrict__ b,
+__device__ __forceinline__ void node_macros_r(const Co<R>& c, bool vh, const S* __restrict__ b,
                                               long long plane, long long i, R& rho, R& ux, R& uy,
                                               R& T) {
   R f[9], s = R(0);
@@ -786,11 +807,11 @@ __device__ __forceinline__ void node_macros_r(const DevCoef& c, const S* __restr
   for (int q = 0; q < 9; ++q) f[q] = (R)to_r(b[q * plane + i]);
 #pragma unroll
   for (int q = 9; q < 14; ++q) s += (R)to_r(b[q * plane + i]);
-  const R qv = c.vh ? (R)to_r(b[14 * plane + i]) : R(0);
-  T = (R)c.T0 + s - R(0.5) * ((R)c.Q + qv);
-  const R Fx = (R)c.Fvx, Fy = (R)c.Fvy + (R)(c.rho0 * c.gbeta) * (T - R(0.5) * qv - (R)c.T0);
+  const R qv = vh ? (R)to_r(b[14 * plane + i]) : R(0);
+  T = c.T0 + s - R(0.5) * (c.Q + qv);
+  const R Fx = c.Fvx, Fy = c.Fvy + c.rgb * (T - R(0.5) * qv - c.T0);
   const R dr = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
-  rho = (R)c.rho0 + dr;
+  rho = c.rho0 + dr;
   const R jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
   const R jy = (f[2] - f[4]) + (f[5] - f[7]) + (f[6] - f[8]);
   const R inv = R(1) / rho;
@@ -995,13 +1016,15 @@ __global__ void __launch_bounds__(kRedThreads)
   // in the collision's arithmetic (FP32 below FP64 storage, where FP64 is
   // slow); block sums in FP64
   using R = typename Traits<S>::R;
+  const Co<R> co = make_co<R>(L->c);
+  const bool vh = L->c.vh != 0;
   R a[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   for (long long k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
     const int y = (int)(k / g.nx), x = (int)(k - (long long)y * g.nx);
     const long long idx = (long long)y * g.pitch + x;
     if (g.flags && (g.flags[idx] & kFlagSolid)) continue;
     R r1, u1, v1, t1;
-    node_macros_r(L->c, cur, g.plane, idx, r1, u1, v1, t1);
+    node_macros_r(co, vh, cur, g.plane, idx, r1, u1, v1, t1);
     const R t0 = (R)snap[k], u0 = (R)snap[n + k], v0 = (R)snap[2 * n + k];
     a[0] += (t1 - t0) * (t1 - t0);
     a[1] += t1 * t1;
