@@ -419,6 +419,96 @@ def run_batch(args):
     return 0
 
 
+def conv_flops_per_train_step(G, cin, cout, base, levels, batch):
+    """Multiply-adds x 2 of every convolution GEMM in one training step: the
+    forward pass, the weight gradients and the input gradients (none for the
+    first layer, whose input is data)."""
+    from paper_1801_04577_gb300.net import layer_shapes
+    shapes = layer_shapes(G, cin, cout, base, levels)
+    # resolution of each layer, in layer order (encoder, bottleneck, decoder, head)
+    res = []
+    for l in range(levels - 1):
+        res += [G >> l, G >> l]
+    res += [G >> (levels - 1)] * 2
+    for l in range(levels - 2, -1, -1):
+        res += [G >> l, G >> l]
+    res.append(G)
+    total = 0.0
+    for li, ((ci, co, k), h) in enumerate(zip(shapes, res)):
+        f = 2.0 * batch * h * h * co * ci * k * k
+        total += f * (2 if li == 0 else 3)
+    return total
+
+
+def run_unet(args):
+    """Training steps of the warm-start U-Net (64^2 grid, widths 24..192,
+    1.1 M parameters, batch 32) on the tensor cores."""
+    import torch
+
+    from paper_1801_04577_gb300.net import Net
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py: no CUDA device (the library has no CPU path)")
+    G, cin, cout, base, levels, B = 64, 5, 3, 24, 4, args.net_batch
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    net = Net(G, cin, cout, base, levels, B, seed=3, stream=stream.cuda_stream, math=args.net_math)
+    r = I.splitmix64_uniform(1801045773, B * (cin + cout + 1) * G * G)
+    o1, o2 = B * cin * G * G, B * (cin + cout) * G * G
+    x = torch.from_numpy((2 * r[:o1] - 1).reshape(B, cin, G, G).astype(np.float32)).cuda()
+    t = torch.from_numpy((2 * r[o1:o2] - 1).reshape(B, cout, G, G).astype(np.float32)).cuda()
+    m = torch.from_numpy((r[o2:] > 0.25).reshape(B, G, G).astype(np.float32)).cuda()
+    for _ in range(args.warmup):
+        net.train_step(x, t, m, 1e-3)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(device_index(0))
+    sampler.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        loss = net.train_step(x, t, m, 1e-3)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    y = torch.empty((B, cout, G, G), dtype=torch.float32, device="cuda")
+    net.forward(x, y)
+    torch.cuda.synchronize()
+    f0 = torch.cuda.Event(enable_timing=True)
+    f1 = torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    for _ in range(20):
+        net.forward(x, y)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    flops = conv_flops_per_train_step(G, cin, cout, base, levels, B)
+    achieved = flops / (ms * 1e-3) / 1e12
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            peak, kind = float(json.load(fh)["bf16_tflops"]), "measured bf16 burst"
+    except Exception:
+        peak, kind = 1900.0, "fallback bf16 burst"
+    line = {"metric": "train_samples_per_s", "value": B * 1000.0 / ms, "unit": "samples/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16 operands, fp32 accumulate" if args.net_math == "tensor" else "fp32",
+            "data": "synthetic",
+            "config": {"workload": f"unet_g{G}_b{base}_l{levels}_batch{B}_{args.net_math}",
+                       "parameters": net.nparam, "forward_ms": f0.elapsed_time(f1) / 20,
+                       "conv_gflop_per_step": flops / 1e9, "loss_last": loss,
+                       "l2": "activations of one batch (~0.3 GB) larger than L2 in the first level"},
+            "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "kernel": "tc::gemm_kernel (all convolution GEMMs of a training step)",
+                         "peak_kind": kind},
+            "gpu_launches": None}
+    if clocks is not None:
+        line["clocks"] = clocks
+    print(json.dumps(line), flush=True)
+    net.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -434,6 +524,8 @@ def main():
     ap.add_argument("--batch-size", type=int, default=512)
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--check-every", type=int, default=100)
+    ap.add_argument("--net-batch", type=int, default=32)
+    ap.add_argument("--net-math", choices=["tensor", "fp32"], default="tensor")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("bench.py: at least 3 warm-up steps are required")
@@ -441,6 +533,8 @@ def main():
         return run_reference(args)
     if args.workload == "batch512":
         return run_batch(args)
+    if args.workload == "unet64":
+        return run_unet(args)
     return run_native(args)
 
 

@@ -118,6 +118,8 @@ static DevGeom make_geom(const clbm_ctx* c) {
   g.lk_tbc = c->d_lk_tbc;
   g.tbc = c->d_tbc;
   std::memcpy(g.side_b, c->side_b, sizeof(g.side_b));
+  for (int sd = 0; sd < 4; ++sd)
+    for (int k = 0; k < 3; ++k) g.side_bf[sd][k] = (float)c->side_b[sd][k];
   return g;
 }
 

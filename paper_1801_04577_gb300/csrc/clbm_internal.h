@@ -32,6 +32,7 @@ struct DevGeom {
   const int32_t* lk_tbc;       // [nslots][4] condition index, -1 = no link
   const double* tbc;           // [ntbc][3] (b1, b2, b3)
   double side_b[4][3];         // conditions of the box sides x0, x1, y0, y1
+  float side_bf[4][3];         // the same rounded to FP32 (for FP32 arithmetic)
 };
 
 // Relaxation and forcing constants in FP64 (converted to the compute type

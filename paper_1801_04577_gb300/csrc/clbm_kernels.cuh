@@ -458,9 +458,15 @@ __device__ __forceinline__ void fixup(const DevGeom& g, const Co<R>& c, const S*
         if (boxwall) {
           const int sd = side_of(j);
           ne = R(1);
-          b1 = (R)g.side_b[sd][0];
-          b2 = (R)g.side_b[sd][1];
-          b3 = (R)g.side_b[sd][2];
+          if constexpr (std::is_same<R, float>::value) {
+            b1 = g.side_bf[sd][0];
+            b2 = g.side_bf[sd][1];
+            b3 = g.side_bf[sd][2];
+          } else {
+            b1 = (R)g.side_b[sd][0];
+            b2 = (R)g.side_b[sd][1];
+            b3 = (R)g.side_b[sd][2];
+          }
         } else {
           const int s = g.slot[own];
           const int t = g.lk_tbc[4 * s + (i - 1)];

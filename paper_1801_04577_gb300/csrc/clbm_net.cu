@@ -180,16 +180,21 @@ struct GatherIm2col {
           ++t;
         }
       }
-    } else {
+    } else {  // channels not a multiple of 8: walk (tap, channel) element by element
+      int t = k0 / C, c = k0 - t * C;
+      int off = (t / KS - R) * x.W + (t % KS - R);
 #pragma unroll 2
       for (int kc = 0; kc < tc::kBK / 8; ++kc) {
         float v[8];
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
-          const int k = k0 + kc * 8 + e;
-          const int t = k / C, c = k - t * C;
-          const bool ok = k < kend && ((vm >> t) & 1u);
-          v[e] = ok ? __ldg(src + c * hw + (t / KS - R) * x.W + (t % KS - R)) : 0.0f;
+          const bool ok = k0 + kc * 8 + e < kend && ((vm >> t) & 1u);
+          v[e] = ok ? __ldg(src + c * hw + off) : 0.0f;
+          if (++c == C) {
+            c = 0;
+            ++t;
+            off = (t / KS - R) * x.W + (t % KS - R);
+          }
         }
         put_chunk(dst, r, kc, v);
       }
@@ -650,12 +655,13 @@ tc::Packed packed_of(const clbm_net* net, int layer, int transpose) {
 
 // K range per split of a weight-gradient GEMM (K = pixels): the FP32 kernel
 // takes 4096 pixels per split; the tensor-core one enough splits to give
-// about two CTAs per SM (a multiple of its 64-wide K slice).
+// about eight CTAs per SM (its gathers are latency-bound), at least four
+// 64-wide K slices each.
 long long dw_kper(bool tensor, long long Np, int Kd, int co) {
   if (!tensor) return 4096;
   const long long tiles = (long long)((Kd + tc::kBM - 1) / tc::kBM) * ((co + tc::kMaxBN - 1) / tc::kMaxBN);
-  long long splits = std::max<long long>(1, (2 * 152 + tiles - 1) / tiles);
-  splits = std::min<long long>(splits, std::max<long long>(1, Np / 512));
+  long long splits = std::max<long long>(1, (8 * 152 + tiles - 1) / tiles);
+  splits = std::min<long long>(splits, std::max<long long>(1, Np / 256));
   const long long per = (Np + splits - 1) / splits;
   return ((per + tc::kBK - 1) / tc::kBK) * tc::kBK;
 }

@@ -60,3 +60,11 @@ def test_launch_count_claim_follows_the_launch_scheme():
     assert bench.step_launches(rb, 10) == 10
     assert bench.step_launches(rb, 64) == 64 + 1 + 2
     assert bench.step_launches(an, 100) == 200 + 1 + 3
+
+
+def test_unet_flop_count_by_hand():
+    """Two-level U-Net on 4^2, one sample: forward GEMM flops counted layer by
+    layer (2 x pixels x co x ci x k^2) = 8128; a training step is three times
+    that minus the first layer's input gradient (576)."""
+    import bench
+    assert bench.conv_flops_per_train_step(4, 1, 1, 2, 2, 1) == 3 * 8128 - 576
