@@ -529,7 +529,7 @@ __device__ __forceinline__ void st1(S* p, R v, int stochastic, uint32_t r) {
 // next to solids come out wrong here and are recomputed afterwards by the
 // boundary kernel from its precomputed node list.  Keeping the walls out of
 // this kernel keeps its warps free of divergent wall code.
-template <typename S, int V, bool SKIP_EDGES = false, bool VH = false>
+template <typename S, int V, bool SKIP_EDGES = false, bool VH = false, bool SKIP_DEAD = true>
 __device__ __forceinline__ void step_tile(const DevGeom& g, const Co<typename Traits<S>::R>& c,
                                           const S* __restrict__ src, S* __restrict__ dst, int y,
                                           int xw, int lane, uint32_t seed, int stochastic) {
@@ -547,6 +547,13 @@ __device__ __forceinline__ void step_tile(const DevGeom& g, const Co<typename Tr
   }
   const int xl = x0 > 0 ? x0 - 1 : 0;
   const int xr = x0 + V < g.pitch ? x0 + V : g.pitch - 1;
+  // SKIP_DEAD: a lane wholly beyond the row (x0 >= nx: the pitch padding of
+  // the last tile) neither loads nor stores; it still takes part in the
+  // shuffles, and the only value it passes on (to node nx - 1 from x = nx)
+  // belongs to the last column, which the boundary update recomputes.  (The
+  // 16-bit single-lattice kernels leave it off: the extra live state costs
+  // them register spills, more than the padding they would skip.)
+  const bool live = !SKIP_DEAD || x0 < g.nx;
 
   R v[14][V];
 #pragma unroll
@@ -556,7 +563,12 @@ __device__ __forceinline__ void step_tile(const DevGeom& g, const Co<typename Tr
     const int row = ey > 0 ? ym : (ey < 0 ? yp : y);
     const S* base = src + q * plane + (long long)row * g.pitch;
     R t[V];
-    ldv<S, V>(base + x0, t);
+    if (live) {
+      ldv<S, V>(base + x0, t);
+    } else {
+#pragma unroll
+      for (int k = 0; k < V; ++k) t[k] = R(0);
+    }
     if (ex == 0) {
 #pragma unroll
       for (int k = 0; k < V; ++k) v[q][k] = t[k];
@@ -568,7 +580,7 @@ __device__ __forceinline__ void step_tile(const DevGeom& g, const Co<typename Tr
       for (int k = 1; k < V; ++k) v[q][k] = t[k - 1];
     } else {  // value from x + 1
       R right = __shfl_down_sync(0xffffffffu, t[0], 1);
-      if (lane == 31) right = to_r(base[xr]);
+      if (lane == 31 && live) right = to_r(base[xr]);
 #pragma unroll
       for (int k = 0; k < V - 1; ++k) v[q][k] = t[k + 1];
       v[q][V - 1] = right;
@@ -590,6 +602,7 @@ __device__ __forceinline__ void step_tile(const DevGeom& g, const Co<typename Tr
     for (int q = 0; q < 5; ++q) v[9 + q][k] = h[q];
   }
 
+  if (!live) return;
   S* out = dst + (long long)y * g.pitch + x0;
   if constexpr (VH) {  // the viscous source of this step, read back with T (15th plane)
     if constexpr (SKIP_EDGES) {
@@ -690,8 +703,9 @@ __global__ void __launch_bounds__(kStepThreads) step_kernel(const StepArgs a) {
   if (xw >= a.g.nx) return;  // whole warps only: the shuffles need all 32 lanes
   const Co<R> c = make_co<R>(a.c);
   const int y = a.reverse ? a.g.ny - 1 - (int)blockIdx.y : (int)blockIdx.y;
-  step_tile<S, V, false, VH>(a.g, c, static_cast<const S*>(a.src), static_cast<S*>(a.dst), y, xw,
-                             lane, step_seed(a), a.stochastic);
+  step_tile<S, V, false, VH, sizeof(S) != 2>(a.g, c, static_cast<const S*>(a.src),
+                                             static_cast<S*>(a.dst), y, xw, lane, step_seed(a),
+                                             a.stochastic);
 }
 
 // The boundary nodes of the same step (launched after step_kernel).
@@ -732,8 +746,9 @@ __global__ void __launch_bounds__(kStepThreads, 5) step_fused_kernel(const StepA
   const int warp = (b % xblocks) * (kStepThreads / 32) + (threadIdx.x >> 5);
   const int xw = warp * 32 * V;
   if (xw >= a.g.nx) return;  // whole warps only
-  step_tile<S, V, true, VH>(a.g, c, static_cast<const S*>(a.src), static_cast<S*>(a.dst), y, xw,
-                            lane, step_seed(a), a.stochastic);
+  step_tile<S, V, true, VH, sizeof(S) != 2>(a.g, c, static_cast<const S*>(a.src),
+                                            static_cast<S*>(a.dst), y, xw, lane, step_seed(a),
+                                            a.stochastic);
 }
 
 // ---------------------------------------------------------------------------
