@@ -61,7 +61,7 @@ def lib():
         ip = C.POINTER(C.c_int32)
         vp = C.c_void_p
         L.oref_create.argtypes = [C.POINTER(OrefParams), C.c_void_p, dp, C.c_int32, ip, ip, ip,
-                                  dp, ip, C.c_int32, C.POINTER(C.c_void_p)]
+                                  dp, ip, dp, C.c_int32, C.POINTER(C.c_void_p)]
         L.oref_create.restype = C.c_int
         L.oref_destroy.argtypes = [vp]
         L.oref_init.argtypes = [vp, dp, dp, dp, dp]
@@ -73,6 +73,10 @@ def lib():
         L.oref_residual.argtypes = [vp, dp]
         L.oref_wall_temperature.argtypes = [C.c_double] * 6 + [C.c_int]
         L.oref_wall_temperature.restype = C.c_double
+        L.oref_wall_temperature_q.argtypes = [C.c_double] * 7 + [C.c_int]
+        L.oref_wall_temperature_q.restype = C.c_double
+        L.oref_midpoint_temperature_q.argtypes = [C.c_double] * 4 + [C.c_int, C.c_double, C.c_int, C.c_int]
+        L.oref_midpoint_temperature_q.restype = C.c_double
         L.oref_moment_matrix.argtypes = [dp]
         L.oref_shift_matrix.argtypes = [C.c_double, C.c_double, dp]
         L.oref_thermal_moment_matrix.argtypes = [dp]
@@ -133,11 +137,13 @@ class Oracle:
         ld = np.ascontiguousarray(geom.link_dir, np.int32)
         le = np.ascontiguousarray(geom.link_ne, np.float64)
         lt = np.ascontiguousarray(geom.link_tbc, np.int32)
+        lq = getattr(geom, "link_q", None)
+        lq = None if lq is None else np.ascontiguousarray(lq, np.float64)
         self.solid = solid
         h = C.c_void_p()
         st = L.oref_create(C.byref(self._p), None if solid is None else solid.ctypes.data,
                            _dp(tbc), tbc.shape[0], _ip(side), _ip(ln), _ip(ld), _dp(le), _ip(lt),
-                           ln.shape[0], C.byref(h))
+                           _dp(lq), ln.shape[0], C.byref(h))
         if st != 0:
             raise ValueError(f"oracle rejected the problem description (status {st})")
         self._h = h
@@ -271,6 +277,17 @@ def thermal_shift_matrix(ux, uy):
 
 def wall_temperature(b1, b2, b3, ne, T1, T2, have_T2=True):
     return lib().oref_wall_temperature(b1, b2, b3, ne, T1, T2, int(have_T2))
+
+
+def wall_temperature_q(b1, b2, b3, ne, q, T1, T2, have_T2=True):
+    """T_w of a wall at the fraction q of the link."""
+    return lib().oref_wall_temperature_q(b1, b2, b3, ne, q, T1, T2, int(have_T2))
+
+
+def midpoint_temperature_q(q, Tw, T1, T2, T3=0.0, have_T2=True, have_T3=True, dirichlet=False):
+    """The wall profile at the link midpoint, the value Eq. 26 imposes there."""
+    return lib().oref_midpoint_temperature_q(q, Tw, T1, T2, int(have_T2), T3, int(have_T3),
+                                             int(dirichlet))
 
 
 def threads() -> int:

@@ -21,6 +21,17 @@
  *     then the wall rules: half-way bounce-back for f (Sec. 3) and the general
  *     bounce-back of Eq. 26 with T_w from Eq. 28 for g.
  *
+ * Walls off the link midpoint (beyond the paper, which places every wall
+ * half-way along its links): a listed link may carry the fraction q of the
+ * link from the fluid node to the wall.  Then f follows the linear
+ * interpolated bounce-back of Bouzidi, Firdaouss and Lallemand (Phys. Fluids
+ * 13, 2001), and g keeps Eq. 26 at the link midpoint with the temperature
+ * that the wall condition implies there: T_w at the wall from the condition
+ * with the gradient of the quadratic through the wall point and the fluid
+ * nodes at distances q and 1 + q (Eq. 27-28 when q = 1/2), and that
+ * quadratic evaluated at the midpoint.  With q = 1/2 every rule is the
+ * paper's.
+ *
  * The state held between steps is the pre-collision pair (f, g) at time t.
  * All arithmetic is double precision; the file is compiled with
  * -ffp-contract=off so that no fused multiply-add changes the rounding.
@@ -172,6 +183,8 @@ typedef struct {
   /* thermal wall data per (node, D2Q5 dir 1..4): tbc index or -1, and n.e  */
   int32_t* wtbc;
   double* wne;
+  double* wq;                  /* per (node, dir 1..8): wall fraction q, 0.5 default */
+  double *fs, *gs;             /* post-collision DFs of every node (one step)  */
   double* tbc;                 /* ntbc x (b1,b2,b3)                         */
   int32_t ntbc;
   double *f, *g, *fn, *gn;     /* pre-collision DFs at t, and at t+1        */
@@ -330,6 +343,59 @@ double oref_wall_temperature(double b1, double b2, double b3, double ne, double 
   return (2.0 * b1 * T1 + ne * b3) / (2.0 * b1 + ne * b2);
 }
 
+/* Walls at the fraction q of the link (beyond the paper).  With s the
+ * distance from the wall along the link into the fluid, T(s) is the quadratic
+ * through (0, T_w), (q, T_1), (1 + q, T_2), so
+ *   dT/ds(0) = -(1+2q)/(q(1+q)) T_w + (1+q)/q T_1 - q/(1+q) T_2
+ * and dT/dn = -dT/ds(0) / (n.e_i).  b1 dT/dn + b2 T_w = b3 is solved for T_w.
+ * Without T_2 the profile is the line through (0, T_w), (q, T_1).  For q = 1/2
+ * these are Eq. 27-28 and their one-sided fallback. */
+double oref_wall_temperature_q(double b1, double b2, double b3, double ne, double q, double T1,
+                               double T2, int have_T2) {
+  if (have_T2) {
+    const double a = (1.0 + 2.0 * q) / (q * (1.0 + q));
+    const double c1 = (1.0 + q) / q, c2 = q / (1.0 + q);
+    return (b3 * ne + b1 * (c1 * T1 - c2 * T2)) / (b1 * a + b2 * ne);
+  }
+  return (b3 * q * ne + b1 * T1) / (b1 + b2 * q * ne);
+}
+
+/* dT/dn at a wall at the fraction q of the link (same profile). */
+static double wall_gradient_q(double ne, double q, double Tw, double T1, double T2, int have_T2) {
+  if (have_T2)
+    return ((1.0 + 2.0 * q) / (q * (1.0 + q)) * Tw - (1.0 + q) / q * T1 + q / (1.0 + q) * T2) / ne;
+  return (Tw - T1) / (q * ne);
+}
+
+/* Value at s of the quadratic through (0, v0), (s1, v1), (s2, v2). */
+static double quad_at(double s, double s1, double s2, double v0, double v1, double v2) {
+  const double l0 = (s - s1) * (s - s2) / (s1 * s2);
+  const double l1 = s * (s - s2) / (s1 * (s1 - s2));
+  const double l2 = s * (s - s1) / (s2 * (s2 - s1));
+  return l0 * v0 + l1 * v1 + l2 * v2;
+}
+
+/* The wall profile at the link midpoint s = q - 1/2, the temperature that
+ * Eq. 26 imposes there.  q >= 1/2: the midpoint lies between the wall and
+ * x_f, and the quadratic through (0, T_w), (q, T_1), (1 + q, T_2) is
+ * interpolated.  q < 1/2: it lies beyond the wall; the quadratic through
+ * (0, T_w), (1 + q, T_2), (2 + q, T_3) is extrapolated instead, which keeps
+ * the weights bounded as q -> 0 and leaves out T_1 (a large weight on the
+ * node's own temperature feeds back into the node and is unstable).  Both are
+ * exact for quadratic profiles.  Fallbacks for thin fluid layers: lines
+ * through the available points, else T_w. */
+double oref_midpoint_temperature_q(double q, double Tw, double T1, double T2, int have_T2, double T3,
+                                   int have_T3, int dirichlet) {
+  const double s = q - 0.5;
+  if (q >= 0.5 || !dirichlet) {
+    if (have_T2) return quad_at(s, q, 1.0 + q, Tw, T1, T2);
+    return Tw + (T1 - Tw) * s / q;
+  }
+  if (have_T2 && have_T3) return quad_at(s, 1.0 + q, 2.0 + q, Tw, T2, T3);
+  if (have_T2) return Tw + (T2 - Tw) * s / (1.0 + q);
+  return Tw;
+}
+
 /* Eq. 27 (or its one-sided fallback). */
 static double wall_gradient(double ne, double Tw, double T1, double T2, int have_T2) {
   if (have_T2) return (8.0 * Tw - 9.0 * T1 + T2) / (3.0 * ne);
@@ -375,6 +441,9 @@ void oref_destroy(void* h) {
   free(c->solid);
   free(c->wtbc);
   free(c->wne);
+  free(c->wq);
+  free(c->fs);
+  free(c->gs);
   free(c->tbc);
   free(c->f);
   free(c->g);
@@ -388,9 +457,13 @@ void oref_destroy(void* h) {
   free(c);
 }
 
+/* Links: node, dir (1..8, from the fluid node towards the wall), n.e_i and
+ * condition index (D2Q5 directions 1..4 only; ignored for 5..8), and the wall
+ * fraction q in (0, 1] (lq NULL: 1/2 for every link). */
 int oref_create(const oref_params* p, const uint8_t* solid, const double* tbc, int32_t ntbc,
                 const int32_t* side_tbc, const int32_t* lnode, const int32_t* ldir,
-                const double* lne, const int32_t* ltbc, int32_t nlinks, void** out) {
+                const double* lne, const int32_t* ltbc, const double* lq, int32_t nlinks,
+                void** out) {
   *out = NULL;
   if (p->nx < 1 || p->ny < 1) return OREF_EINVAL;
   oref_ctx* c = (oref_ctx*)calloc(1, sizeof(oref_ctx));
@@ -417,9 +490,12 @@ int oref_create(const oref_params* p, const uint8_t* solid, const double* tbc, i
   c->solid = (uint8_t*)calloc(n, 1);
   c->wtbc = (int32_t*)malloc(5 * n * sizeof(int32_t));
   c->wne = (double*)calloc(5 * n, sizeof(double));
+  c->wq = (double*)malloc(9 * n * sizeof(double));
+  c->fs = (double*)calloc(9 * n, sizeof(double));
+  c->gs = (double*)calloc(5 * n, sizeof(double));
   c->tbc = (double*)calloc(3 * (ntbc > 0 ? ntbc : 1), sizeof(double));
   if (!c->f || !c->g || !c->fn || !c->gn || !c->T || !c->rho || !c->ux || !c->uy || !c->Qn || !c->solid ||
-      !c->wtbc || !c->wne || !c->tbc) {
+      !c->wtbc || !c->wne || !c->wq || !c->fs || !c->gs || !c->tbc) {
     oref_destroy(c);
     return OREF_ENOMEM;
   }
@@ -427,6 +503,7 @@ int oref_create(const oref_params* p, const uint8_t* solid, const double* tbc, i
   c->ntbc = ntbc;
   if (ntbc > 0) memcpy(c->tbc, tbc, 3 * ntbc * sizeof(double));
   for (int64_t k = 0; k < 5 * n; ++k) c->wtbc[k] = -1;
+  for (int64_t k = 0; k < 9 * n; ++k) c->wq[k] = 0.5;
   /* Box sides: axis-aligned links, n.e_i = 1. */
   for (int y = 0; y < p->ny; ++y)
     for (int x = 0; x < p->nx; ++x) {
@@ -446,13 +523,18 @@ int oref_create(const oref_params* p, const uint8_t* solid, const double* tbc, i
     }
   /* Listed links into solid nodes. */
   for (int32_t l = 0; l < nlinks; ++l) {
-    if (lnode[l] < 0 || lnode[l] >= n || ldir[l] < 1 || ldir[l] > 4 || ltbc[l] < 0 ||
-        ltbc[l] >= ntbc || !(lne[l] > 0)) {
+    const double q = lq ? lq[l] : 0.5;
+    const int axis = ldir[l] >= 1 && ldir[l] <= 4;
+    if (lnode[l] < 0 || lnode[l] >= n || ldir[l] < 1 || ldir[l] > 8 || !(q > 0.0 && q <= 1.0) ||
+        (axis && (ltbc[l] < 0 || ltbc[l] >= ntbc || !(lne[l] > 0)))) {
       oref_destroy(c);
       return OREF_EINVAL;
     }
-    c->wtbc[5 * (int64_t)lnode[l] + ldir[l]] = ltbc[l];
-    c->wne[5 * (int64_t)lnode[l] + ldir[l]] = lne[l];
+    if (axis) {
+      c->wtbc[5 * (int64_t)lnode[l] + ldir[l]] = ltbc[l];
+      c->wne[5 * (int64_t)lnode[l] + ldir[l]] = lne[l];
+    }
+    c->wq[9 * (int64_t)lnode[l] + ldir[l]] = q;
   }
   /* Every D2Q5 link from a fluid node into a solid node needs a condition. */
   for (int y = 0; y < p->ny; ++y)
@@ -523,7 +605,20 @@ static void step_once(oref_ctx* c) {
       macros(c, c->f + 9 * k, c->g + 5 * k, &c->rho[k], &c->ux[k], &c->uy[k], &c->T[k], &Fx, &Fy,
              &c->Qn[k]);
     }
-  /* collide, stream (Eq. 11, 21) and apply the wall rules */
+  /* collide every fluid node (Eq. 7-11, Eq. 18-23) */
+#pragma omp parallel for schedule(static) if (c->n >= 2048)
+  for (int y = 0; y < ny; ++y)
+    for (int x = 0; x < nx; ++x) {
+      int64_t k = idx(c, x, y);
+      if (!is_fluid(c, x, y)) continue;
+      const double Fx = c->p.Fvx;
+      /* force temperature: T without the viscous source's half (see macros) */
+      const double Tf = c->T[k] - 0.5 * (c->Qn[k] - c->p.Q);
+      const double Fy = c->p.Fvy + c->p.rho0 * c->p.gbeta * (Tf - c->p.T0);
+      collide_flow(c, c->f + 9 * k, c->rho[k], c->ux[k], c->uy[k], Fx, Fy, c->fs + 9 * k);
+      collide_thermal(c, c->g + 5 * k, c->ux[k], c->uy[k], c->T[k], c->Qn[k], c->gs + 5 * k);
+    }
+  /* stream (Eq. 11, 21) and apply the wall rules */
 #pragma omp parallel for schedule(static) if (c->n >= 2048)
   for (int y = 0; y < ny; ++y)
     for (int x = 0; x < nx; ++x) {
@@ -533,37 +628,53 @@ static void step_once(oref_ctx* c) {
         for (int i = 0; i < 5; ++i) c->gn[5 * k + i] = 0.0;
         continue;
       }
-      double fs[9], gs[5];
-      const double Fx = c->p.Fvx;
-      /* force temperature: T without the viscous source's half (see macros) */
-      const double Tf = c->T[k] - 0.5 * (c->Qn[k] - c->p.Q);
-      const double Fy = c->p.Fvy + c->p.rho0 * c->p.gbeta * (Tf - c->p.T0);
-      collide_flow(c, c->f + 9 * k, c->rho[k], c->ux[k], c->uy[k], Fx, Fy, fs);
-      collide_thermal(c, c->g + 5 * k, c->ux[k], c->uy[k], c->T[k], c->Qn[k], gs);
+      const double* fs = c->fs + 9 * k;
+      const double* gs = c->gs + 5 * k;
       for (int i = 0; i < 9; ++i) {
         int xo, yo, side;
         if (neighbour(c, x, y, EX[i], EY[i], &xo, &yo, &side) && is_fluid(c, xo, yo)) {
           c->fn[9 * idx(c, xo, yo) + i] = fs[i];
-        } else {
+          continue;
+        }
+        const double q = c->wq[9 * k + i];
+        int xb, yb, sb;
+        const int have_b = neighbour(c, x, y, -EX[i], -EY[i], &xb, &yb, &sb) && is_fluid(c, xb, yb);
+        if (q == 0.5 || (q < 0.5 && !have_b)) {
           /* half-way bounce-back: the DF returns to x_f reversed */
           c->fn[9 * k + opp[i]] = fs[i];
+        } else if (q < 0.5) {
+          /* f_i* interpolated to the point 1 - 2q behind x_f, which reaches x_f reflected */
+          c->fn[9 * k + opp[i]] = 2.0 * q * fs[i] + (1.0 - 2.0 * q) * c->fs[9 * idx(c, xb, yb) + i];
+        } else {
+          /* the reflected DF lands 2q - 1 beyond x_f: interpolate with f_ibar* at x_f */
+          c->fn[9 * k + opp[i]] = fs[i] / (2.0 * q) + (2.0 * q - 1.0) / (2.0 * q) * fs[opp[i]];
         }
       }
       for (int i = 0; i < 5; ++i) {
         int xo, yo, side;
         if (neighbour(c, x, y, EX[i], EY[i], &xo, &yo, &side) && is_fluid(c, xo, yo)) {
           c->gn[5 * idx(c, xo, yo) + i] = gs[i];
-        } else {
-          /* Eq. 26-28 with e_i pointing into the wall */
-          const int t = c->wtbc[5 * k + i];
-          const double ne = c->wne[5 * k + i];
-          const double* b = c->tbc + 3 * t;
-          int x2, y2, s2;
-          int have2 = neighbour(c, x, y, -EX[i], -EY[i], &x2, &y2, &s2) && is_fluid(c, x2, y2);
-          const double T2 = have2 ? c->T[idx(c, x2, y2)] : 0.0;
-          const double Tw = oref_wall_temperature(b[0], b[1], b[2], ne, c->T[k], T2, have2);
-          c->gn[5 * k + opp[i]] = -gs[i] + cT2 * Tw;
+          continue;
         }
+        /* Eq. 26-28 with e_i pointing into the wall */
+        const int t = c->wtbc[5 * k + i];
+        const double ne = c->wne[5 * k + i];
+        const double* b = c->tbc + 3 * t;
+        const double q = c->wq[9 * k + i];
+        int x2, y2, s2;
+        int have2 = neighbour(c, x, y, -EX[i], -EY[i], &x2, &y2, &s2) && is_fluid(c, x2, y2);
+        const double T2 = have2 ? c->T[idx(c, x2, y2)] : 0.0;
+        double Tm;
+        if (q == 0.5) {
+          Tm = oref_wall_temperature(b[0], b[1], b[2], ne, c->T[k], T2, have2);
+        } else {
+          int x3 = 0, y3 = 0, s3 = 0;
+          const int have3 = have2 && neighbour(c, x2, y2, -EX[i], -EY[i], &x3, &y3, &s3) && is_fluid(c, x3, y3);
+          const double T3 = have3 ? c->T[idx(c, x3, y3)] : 0.0;
+          const double Tw = oref_wall_temperature_q(b[0], b[1], b[2], ne, q, c->T[k], T2, have2);
+          Tm = oref_midpoint_temperature_q(q, Tw, c->T[k], T2, have2, T3, have3, b[0] == 0.0);
+        }
+        c->gn[5 * k + opp[i]] = -gs[i] + cT2 * Tm;
       }
     }
   double* t;
@@ -637,8 +748,14 @@ int oref_nusselt(void* h, int32_t which, double length, double dT, double* nu) {
         int x2, y2, s2;
         int have2 = neighbour(c, x, y, -EX[i], -EY[i], &x2, &y2, &s2) && is_fluid(c, x2, y2);
         const double T2 = have2 ? T[idx(c, x2, y2)] : 0.0;
-        const double Tw = oref_wall_temperature(b[0], b[1], b[2], ne, T[k], T2, have2);
-        sum += wall_gradient(ne, Tw, T[k], T2, have2);
+        const double q = c->wq[9 * k + i];
+        if (q == 0.5) {
+          const double Tw = oref_wall_temperature(b[0], b[1], b[2], ne, T[k], T2, have2);
+          sum += wall_gradient(ne, Tw, T[k], T2, have2);
+        } else {
+          const double Tw = oref_wall_temperature_q(b[0], b[1], b[2], ne, q, T[k], T2, have2);
+          sum += wall_gradient_q(ne, q, Tw, T[k], T2, have2);
+        }
         cnt += 1;
       }
     }

@@ -80,10 +80,18 @@ class Geometry:
     link_dir: np.ndarray = dataclasses.field(default_factory=lambda: np.zeros(0, np.int32))
     link_ne: np.ndarray = dataclasses.field(default_factory=lambda: np.zeros(0, np.float64))
     link_tbc: np.ndarray = dataclasses.field(default_factory=lambda: np.zeros(0, np.int32))
+    # fraction q in (0, 1] of each link from the fluid node to the wall; None = 1/2 for
+    # every link (the paper's half-way walls).  Links of directions 5..8 carry only q.
+    link_q: Optional[np.ndarray] = None
 
     @property
     def n_links(self) -> int:
         return int(self.link_node.shape[0])
+
+    def link_q_or_half(self) -> np.ndarray:
+        if self.link_q is None:
+            return np.full(self.n_links, 0.5)
+        return np.ascontiguousarray(self.link_q, np.float64)
 
 
 @dataclasses.dataclass
@@ -222,7 +230,7 @@ def _ratio_fraction(ratio: float) -> Fraction:
 
 def annulus(n: int = 2048, ratio: float = 2.6, Ra: float = 1e5, Pr: float = 0.71, U: float = 0.1,
             T_in: float = 1.0, robin_b3: float = 0.0, gravity: bool = True,
-            Q: float = 0.0, alpha: Optional[float] = None) -> Workload:
+            Q: float = 0.0, alpha: Optional[float] = None, interpolated: bool = False) -> Workload:
     """Annulus between concentric cylinders inside an n x n box.
 
     Centre c = ((n-1)/2, (n-1)/2), outer radius ro = n/2 - 1, inner radius
@@ -230,7 +238,10 @@ def annulus(n: int = 2048, ratio: float = 2.6, Ra: float = 1e5, Pr: float = 0.71
     b2 = 1/(ro - ri), b3 = robin_b3.  Fluid/solid classification is done in
     exact integer arithmetic on doubled coordinates, so it is reproducible.
     Wall links carry n.e_i with n the outward (fluid -> wall) unit normal of
-    the circle at the point where the link crosses it.
+    the circle at the point where the link crosses it.  interpolated=True
+    also lists the diagonal links and gives every link the fraction q at
+    which it crosses the circle; otherwise the walls are half-way (the
+    paper's staircase).
     """
     ro = n / 2.0 - 1.0
     fr = _ratio_fraction(ratio)
@@ -253,9 +264,9 @@ def annulus(n: int = 2048, ratio: float = 2.6, Ra: float = 1e5, Pr: float = 0.71
     p = Params(nx=n, ny=n, s_nu=s_nu, lambda1=lambda1, T0=0.5, gbeta=gbeta, Q=Q)
     tbc = [dirichlet(T_in), robin(1.0, 1.0 / H, robin_b3)]
     c = (n - 1) / 2.0
-    nodes, dirs, nes, tbcs = [], [], [], []
+    nodes, dirs, nes, tbcs, qs = [], [], [], [], []
     ys, xs = np.nonzero(fluid)
-    for d in (1, 2, 3, 4):
+    for d in ((1, 2, 3, 4, 5, 6, 7, 8) if interpolated else (1, 2, 3, 4)):
         ex, ey = EX[d], EY[d]
         xn, yn = xs + ex, ys + ey
         inb = (xn >= 0) & (xn < n) & (yn >= 0) & (yn < n)
@@ -285,16 +296,20 @@ def annulus(n: int = 2048, ratio: float = 2.6, Ra: float = 1e5, Pr: float = 0.71
             ne = nx_ * ex + ny_ * ey
             nodes.append(int(y) * n + int(x))
             dirs.append(d)
-            nes.append(max(ne, 1e-3))
-            tbcs.append(0 if inner else 1)
+            # diagonal links carry only q (the thermal lattice has no diagonal links)
+            nes.append(max(ne, 1e-3) if d <= 4 else 0.0)
+            tbcs.append((0 if inner else 1) if d <= 4 else -1)
+            qs.append(min(max(s, 1e-3), 1.0))
     order = np.lexsort((np.asarray(dirs), np.asarray(nodes)))
     g = Geometry(tbc=tbc, side_tbc=(1, 1, 1, 1), solid=solid,
                  link_node=np.asarray(nodes, np.int32)[order],
                  link_dir=np.asarray(dirs, np.int32)[order],
                  link_ne=np.asarray(nes, np.float64)[order],
-                 link_tbc=np.asarray(tbcs, np.int32)[order])
+                 link_tbc=np.asarray(tbcs, np.int32)[order],
+                 link_q=np.asarray(qs, np.float64)[order] if interpolated else None)
     T = np.full((n, n), 0.5)
-    return Workload(f"annulus_{n}x{n}_ratio{ratio:g}", p, g, Fields(T=T), length=H, dT=1.0)
+    name = f"annulus_{n}x{n}_ratio{ratio:g}" + ("_interpolated" if interpolated else "")
+    return Workload(name, p, g, Fields(T=T), length=H, dT=1.0)
 
 
 def axis_links(solid: np.ndarray, tbc_index: int) -> Tuple[np.ndarray, np.ndarray, np.ndarray, np.ndarray]:
@@ -350,6 +365,64 @@ def poiseuille_channel(ny: int = 8, nu: float = 0.1, Fx: float = 1e-5, nx: int =
     g = Geometry(tbc=[dirichlet(Tw)], side_tbc=(-1, -1, 0, 0))
     return Workload(f"poiseuille_{ny}", p, g, Fields(T=np.full((ny, nx), Tw)), length=float(ny),
                     u_scale=Fx * ny * ny / (8.0 * nu))
+
+
+def offset_channel(N: int = 8, q_bottom: float = 0.3, q_top: float = 0.8, nu: float = 0.1,
+                   alpha: float = 0.1, Fx: float = 1e-5, T_bottom: float = 1.0, T_top: float = 0.0,
+                   nx: int = 4, top_tbc: Optional[Tuple[float, float, float]] = None,
+                   Q: float = 0.0) -> Workload:
+    """Channel whose walls are not half-way between nodes: solid rows y = 0 and
+    y = N + 1, fluid rows 1..N, the bottom wall at y = 1 - q_bottom and the top
+    wall at y = N + q_top (every link into a wall row, diagonal ones included,
+    carries that fraction); periodic in x and y; body force Fx, uniform heat
+    source Q, no gravity; Dirichlet T_bottom at the bottom, T_top or the
+    condition top_tbc = (b1, b2, b3) at the top.  offset_channel_exact gives
+    the steady solution."""
+    ny = N + 2
+    s_nu, lambda1 = rates_from_diffusivities(nu, alpha)
+    p = Params(nx=nx, ny=ny, periodic_x=1, periodic_y=1, s_nu=s_nu, lambda1=lambda1, Fvx=Fx,
+               T0=0.5 * (T_bottom + T_top), Q=Q)
+    solid = np.zeros((ny, nx), np.uint8)
+    solid[0, :] = 1
+    solid[ny - 1, :] = 1
+    nodes, dirs, nes, tbcs, qs = [], [], [], [], []
+    for x in range(nx):
+        for d in (4, 7, 8):  # into the bottom wall row
+            nodes.append(nx + x); dirs.append(d); qs.append(q_bottom)
+            nes.append(1.0 if d == 4 else 0.0); tbcs.append(0 if d == 4 else -1)
+        for d in (2, 5, 6):  # into the top wall row
+            nodes.append(N * nx + x); dirs.append(d); qs.append(q_top)
+            nes.append(1.0 if d == 2 else 0.0); tbcs.append(1 if d == 2 else -1)
+    order = np.lexsort((np.asarray(dirs), np.asarray(nodes)))
+    top = dirichlet(T_top) if top_tbc is None else robin(*top_tbc)
+    g = Geometry(tbc=[dirichlet(T_bottom), top], side_tbc=(-1, -1, -1, -1), solid=solid,
+                 link_node=np.asarray(nodes, np.int32)[order], link_dir=np.asarray(dirs, np.int32)[order],
+                 link_ne=np.asarray(nes, np.float64)[order], link_tbc=np.asarray(tbcs, np.int32)[order],
+                 link_q=np.asarray(qs, np.float64)[order])
+    L = N + q_top - (1.0 - q_bottom)
+    return Workload(f"offset_channel_{N}_q{q_bottom:g}_{q_top:g}", p, g,
+                    Fields(T=np.full((ny, nx), p.T0)), length=L, u_scale=Fx * L * L / (8.0 * nu))
+
+
+def offset_channel_exact(w: Workload, nu: float, alpha: float, T_bottom: float = 1.0):
+    """(u_x, T) at rows 0..ny-1 of offset_channel (rows 0 and ny-1 are solid):
+    u = Fx/(2 nu) (y - yb)(yt - y); with x = y - yb and L = yt - yb,
+    T = T_bottom + s x + Q/(2 alpha) x (L - x), s fixed by the top condition
+    b1 T'(L) + b2 T(L) = b3 (n = +y there)."""
+    ny = w.params.ny
+    N = ny - 2
+    q, dirs = w.geom.link_q, w.geom.link_dir
+    yb, yt = 1.0 - float(q[dirs == 4][0]), N + float(q[dirs == 2][0])
+    L = yt - yb
+    Fx, Q = w.params.Fvx, w.params.Q
+    y = np.arange(ny, dtype=np.float64)
+    u = Fx / (2.0 * nu) * (y - yb) * (yt - y)
+    b1, b2, b3 = w.geom.tbc[1]
+    c = Q / (2.0 * alpha)
+    # b1 (s - c L) + b2 (T_bottom + s L) = b3
+    s = (b3 - b2 * T_bottom + b1 * c * L) / (b1 + b2 * L)
+    x = y - yb
+    return u, T_bottom + s * x + c * x * (L - x)
 
 
 def dissipation_channel(L: int = 16, nu: float = 0.1, alpha: float = 0.1, Fx: float = 1e-5,
