@@ -101,14 +101,25 @@ typedef struct {
   double b1, b2, b3;
 } clbm_tbc;
 
-/* One wall link of a fluid node into a solid node (Eq. 26-28): the D2Q5 link
- * `dir` (1..4) leaves fluid node `node` = y*nx + x towards the wall (the e_i
- * of Eq. 26), `n_dot_e` = n.e_i > 0 of Eq. 27-28, `tbc` indexes the condition
- * table.  Curved walls are described by such links with the true normal. */
+/* One wall link of a fluid node into a solid node (Eq. 26-28): the link `dir`
+ * leaves fluid node `node` = y*nx + x towards the wall (the e_i of Eq. 26).
+ * D2Q5 directions 1..4: `n_dot_e` = n.e_i > 0 of Eq. 27-28 and `tbc` indexes
+ * the condition table; every D2Q5 link into a solid node must be listed.
+ * Curved walls are described by such links with the true normal.
+ * `q` in (0, 1] is the fraction of the link from the fluid node to the wall.
+ * q = 1/2 is the paper's half-way wall.  Any other q (no counterpart in the
+ * paper) selects, for that link: for f the linear interpolated bounce-back of
+ * Bouzidi, Firdaouss and Lallemand (2001) (q < 1/2 also reads f_i* at
+ * x_f - e_i); for g Eq. 26 at the link midpoint with the temperature that the
+ * wall profile has there (T_w from b1 dT/dn + b2 T_w = b3 with the gradient
+ * of the quadratic through the wall and the fluid nodes at q and 1 + q).
+ * Diagonal directions 5..8 may be listed to give their q (n_dot_e and tbc are
+ * ignored there); unlisted wall directions are half-way. */
 typedef struct {
   int32_t node, dir;
   double n_dot_e;
   int32_t tbc, reserved;
+  double q;
 } clbm_link;
 
 typedef struct clbm_ctx clbm_ctx;

@@ -38,7 +38,7 @@ class clbm_tbc(C.Structure):
 
 class clbm_link(C.Structure):
     _fields_ = [("node", C.c_int32), ("dir", C.c_int32), ("n_dot_e", C.c_double),
-                ("tbc", C.c_int32), ("reserved", C.c_int32)]
+                ("tbc", C.c_int32), ("reserved", C.c_int32), ("q", C.c_double)]
 
 
 class clbm_batch_item(C.Structure):
@@ -154,7 +154,7 @@ def clbm_create(params: clbm_params, stream: Optional[int] = None) -> C.c_void_p
 
 
 def clbm_set_boundaries(ctx, solid: Optional[np.ndarray], tbc: Sequence, side_tbc: Sequence[int],
-                        link_node=None, link_dir=None, link_ne=None, link_tbc=None):
+                        link_node=None, link_dir=None, link_ne=None, link_tbc=None, link_q=None):
     L = load()
     n_tbc = len(tbc)
     tarr = (clbm_tbc * max(n_tbc, 1))(*[clbm_tbc(*map(float, t)) for t in tbc])
@@ -162,7 +162,8 @@ def clbm_set_boundaries(ctx, solid: Optional[np.ndarray], tbc: Sequence, side_tb
     n_links = 0 if link_node is None else int(len(link_node))
     larr = (clbm_link * max(n_links, 1))()
     for k in range(n_links):
-        larr[k] = clbm_link(int(link_node[k]), int(link_dir[k]), float(link_ne[k]), int(link_tbc[k]), 0)
+        larr[k] = clbm_link(int(link_node[k]), int(link_dir[k]), float(link_ne[k]), int(link_tbc[k]), 0,
+                            0.5 if link_q is None else float(link_q[k]))
     sol = None
     if solid is not None:
         sol = np.ascontiguousarray(solid, dtype=np.uint8)
@@ -244,7 +245,7 @@ class Solver:
         self.ctx = clbm_create(make_params(params, precision, rounding), stream)
         if geom is not None:
             clbm_set_boundaries(self.ctx, geom.solid, geom.tbc, geom.side_tbc, geom.link_node,
-                                geom.link_dir, geom.link_ne, geom.link_tbc)
+                                geom.link_dir, geom.link_ne, geom.link_tbc, geom.link_q_or_half())
         if init is not None:
             self.init(init)
 
@@ -355,9 +356,10 @@ class Batch:
             tbc = (clbm_tbc * max(len(g.tbc), 1))(*[clbm_tbc(*map(float, t)) for t in g.tbc])
             nl = g.n_links
             links = (clbm_link * max(nl, 1))()
+            lq = g.link_q_or_half()
             for k in range(nl):
                 links[k] = clbm_link(int(g.link_node[k]), int(g.link_dir[k]), float(g.link_ne[k]),
-                                     int(g.link_tbc[k]), 0)
+                                     int(g.link_tbc[k]), 0, float(lq[k]))
             solid = None if g.solid is None else np.ascontiguousarray(g.solid, np.uint8)
             fields = []
             for a in (w.init.rho, w.init.ux, w.init.uy, w.init.T):

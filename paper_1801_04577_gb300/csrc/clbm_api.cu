@@ -49,6 +49,7 @@ struct clbm_ctx {
   int32_t* d_slot = nullptr;
   double* d_lk_ne = nullptr;
   int32_t* d_lk_tbc = nullptr;
+  double* d_lk_q = nullptr;
   double* d_tbc = nullptr;
   std::vector<int32_t> h_bnodes;  // nodes the boundary kernel recomputes (pitch layout)
   int32_t* d_bnodes = nullptr;
@@ -116,6 +117,7 @@ static DevGeom make_geom(const clbm_ctx* c) {
   g.slot = c->d_slot;
   g.lk_ne = c->d_lk_ne;
   g.lk_tbc = c->d_lk_tbc;
+  g.lk_q = c->d_lk_q;
   g.tbc = c->d_tbc;
   std::memcpy(g.side_b, c->side_b, sizeof(g.side_b));
   for (int sd = 0; sd < 4; ++sd)
@@ -150,6 +152,7 @@ static void free_tables(clbm_ctx* c) {
   cudaFree(c->d_slot);
   cudaFree(c->d_lk_ne);
   cudaFree(c->d_lk_tbc);
+  cudaFree(c->d_lk_q);
   cudaFree(c->d_tbc);
   cudaFree(c->d_bnodes);
   c->d_bnodes = nullptr;
@@ -157,6 +160,7 @@ static void free_tables(clbm_ctx* c) {
   c->d_slot = nullptr;
   c->d_lk_ne = nullptr;
   c->d_lk_tbc = nullptr;
+  c->d_lk_q = nullptr;
   c->d_tbc = nullptr;
   for (auto& kv : c->nu_lists) cudaFree(kv.second.first);
   c->nu_lists.clear();
@@ -344,12 +348,14 @@ clbm_status clbm_set_boundaries(clbm_ctx* c, const uint8_t* solid, const clbm_tb
     std::vector<int32_t> slot_of;  // dense [ny][nx]
     std::vector<double> lk_ne;
     std::vector<int32_t> lk_tbc;
+    std::vector<double> lk_q;  // 8 per slot
     const bool masked = !sol.empty() || n_links > 0;
     if (masked) slot_of.assign((size_t)n, -1);
     for (int l = 0; l < n_links; ++l) {
       const clbm_link& k = links[l];
-      if (k.node < 0 || k.node >= n || k.dir < 1 || k.dir > 4 || k.tbc < 0 || k.tbc >= n_tbc ||
-          !(k.n_dot_e > 0) || !std::isfinite(k.n_dot_e))
+      const bool axis = k.dir >= 1 && k.dir <= 4;
+      if (k.node < 0 || k.node >= n || k.dir < 1 || k.dir > 8 || !(k.q > 0.0 && k.q <= 1.0) ||
+          (axis && (k.tbc < 0 || k.tbc >= n_tbc || !(k.n_dot_e > 0) || !std::isfinite(k.n_dot_e))))
         return fail(c, CLBM_EINVAL, "bad wall link " + std::to_string(l));
       const int x = (int)(k.node % nx), y = (int)(k.node / nx);
       if (is_solid(x, y)) return fail(c, CLBM_EINVAL, "wall link from a solid node");
@@ -358,9 +364,13 @@ clbm_status clbm_set_boundaries(clbm_ctx* c, const uint8_t* solid, const clbm_tb
         s = (int32_t)(lk_tbc.size() / 4);
         lk_ne.insert(lk_ne.end(), 4, 0.0);
         lk_tbc.insert(lk_tbc.end(), 4, -1);
+        lk_q.insert(lk_q.end(), 8, 0.5);
       }
-      lk_ne[4 * s + k.dir - 1] = k.n_dot_e;
-      lk_tbc[4 * s + k.dir - 1] = k.tbc;
+      if (axis) {
+        lk_ne[4 * s + k.dir - 1] = k.n_dot_e;
+        lk_tbc[4 * s + k.dir - 1] = k.tbc;
+      }
+      lk_q[8 * s + k.dir - 1] = k.q;
     }
     std::vector<uint16_t> flags;
     std::vector<int32_t> slot_pitch;
@@ -422,10 +432,13 @@ clbm_status clbm_set_boundaries(clbm_ctx* c, const uint8_t* solid, const clbm_tb
       const size_t ns = std::max<size_t>(lk_tbc.size(), 4);
       lk_ne.resize(ns, 0.0);
       lk_tbc.resize(ns, -1);
+      lk_q.resize(2 * ns, 0.5);
       CLBM_CUDA(c, cudaMalloc(&c->d_lk_ne, ns * sizeof(double)));
       CLBM_CUDA(c, cudaMalloc(&c->d_lk_tbc, ns * sizeof(int32_t)));
+      CLBM_CUDA(c, cudaMalloc(&c->d_lk_q, 2 * ns * sizeof(double)));
       CLBM_CUDA(c, cudaMemcpy(c->d_lk_ne, lk_ne.data(), ns * sizeof(double), cudaMemcpyHostToDevice));
       CLBM_CUDA(c, cudaMemcpy(c->d_lk_tbc, lk_tbc.data(), ns * sizeof(int32_t), cudaMemcpyHostToDevice));
+      CLBM_CUDA(c, cudaMemcpy(c->d_lk_q, lk_q.data(), 2 * ns * sizeof(double), cudaMemcpyHostToDevice));
     }
     {
       std::vector<double> t3((size_t)std::max(n_tbc, 1) * 3, 0.0);
@@ -646,12 +659,13 @@ clbm_status clbm_nusselt(clbm_ctx* c, int32_t which, double length, double dT, d
           L.b1 = b.b1;
           L.b2 = b.b2;
           L.b3 = b.b3;
+          L.q = 0.5;
           v.push_back(L);
         }
       } else {
         const int t = which - 4;
         for (const clbm_link& k : c->h_links) {
-          if (k.tbc != t) continue;
+          if (k.dir > 4 || k.tbc != t) continue;  // diagonal links carry only q
           const int x = (int)(k.node % nx), y = (int)(k.node / nx);
           const clbm_tbc& b = c->h_tbc[t];
           NuLink L;
@@ -661,6 +675,7 @@ clbm_status clbm_nusselt(clbm_ctx* c, int32_t which, double length, double dT, d
           L.b1 = b.b1;
           L.b2 = b.b2;
           L.b3 = b.b3;
+          L.q = k.q;
           v.push_back(L);
         }
       }

@@ -30,6 +30,7 @@ struct DevGeom {
   const int32_t* slot;         // [ny][pitch] link slot, -1 = none (masked lattices)
   const double* lk_ne;         // [nslots][4] n.e_i per link direction i = 1..4
   const int32_t* lk_tbc;       // [nslots][4] condition index, -1 = no link
+  const double* lk_q;          // [nslots][8] wall fraction q per link direction i = 1..8 (0.5 = half-way)
   const double* tbc;           // [ntbc][3] (b1, b2, b3)
   double side_b[4][3];         // conditions of the box sides x0, x1, y0, y1
   float side_bf[4][3];         // the same rounded to FP32 (for FP32 arithmetic)
@@ -96,6 +97,7 @@ struct StepArgs {
 struct NuLink {
   long long own, second;
   double ne, b1, b2, b3;
+  double q;  // wall fraction of the link (0.5 = half-way)
 };
 
 // ---------------------------------------------------------------------------

@@ -421,6 +421,55 @@ __host__ __device__ __forceinline__ R wall_temperature(R b1, R b2, R b3, R ne, R
   return (R(2) * b1 * T1 + ne * b3) / (R(2) * b1 + ne * b2);
 }
 
+// Walls at the fraction q of a link (no counterpart in the paper; q = 1/2 is
+// its half-way wall).  s = distance from the wall along the link into the
+// fluid; the wall profile is the quadratic through (0, T_w), (q, T1),
+// (1 + q, T2), i.e. q(1+q) dT/ds(0) = -(1+2q) T_w + (1+q)^2 T1 - q^2 T2, and
+// dT/dn = -dT/ds(0) / (n.e).  T_w solves b1 dT/dn + b2 T_w = b3 (the line
+// through (0, T_w), (q, T1) when T2 is missing).
+template <typename R>
+__host__ __device__ __forceinline__ R wall_temperature_q(R b1, R b2, R b3, R ne, R q, R T1, R T2, bool have2) {
+  if (have2) {
+    const R qq = q * (R(1) + q), p = R(1) + q;
+    return (b3 * qq * ne + b1 * (p * p * T1 - q * q * T2)) / (b1 * (R(1) + R(2) * q) + b2 * qq * ne);
+  }
+  return (b3 * q * ne + b1 * T1) / (b1 + b2 * q * ne);
+}
+
+// dT/dn at such a wall from the same profile.
+template <typename R>
+__host__ __device__ __forceinline__ R wall_gradient_q(R ne, R q, R Tw, R T1, R T2, bool have2) {
+  if (have2) {
+    const R p = R(1) + q;
+    return ((R(1) + R(2) * q) * Tw - p * p * T1 + q * q * T2) / (q * p * ne);
+  }
+  return (Tw - T1) / (q * ne);
+}
+
+// The profile's value at the link midpoint s = q - 1/2, which Eq. 26 then
+// imposes there.  q >= 1/2 or a wall with a flux term (b1 > 0): interpolation
+// weights of the quadratic through the wall and the nodes at q and 1 + q.
+// q < 1/2 at a Dirichlet wall: the quadratic through the wall and the nodes
+// at 1 + q and 2 + q instead (bounded weights as q -> 0, none on the node's
+// own T1, which would feed back into the node).  Both exact for quadratic
+// profiles; lines through the available points in thin fluid layers.
+template <typename R>
+__host__ __device__ __forceinline__ R midpoint_temperature_q(R q, R Tw, R T1, R T2, bool have2, R T3,
+                                                             bool have3, bool dirichlet) {
+  const R m = R(2) * q - R(1);  // 2 (q - 1/2)
+  if (q >= R(0.5) || !dirichlet) {
+    if (!have2) return Tw + (T1 - Tw) * m / (R(2) * q);
+    const R p = R(1) + q;
+    return R(3) / (R(4) * q * p) * Tw + R(3) * m / (R(4) * q) * T1 - m / (R(4) * p) * T2;
+  }
+  if (have2 && have3) {
+    const R p1 = R(1) + q, p2 = R(2) + q;
+    return R(15) / (R(4) * p1 * p2) * Tw + R(5) * m / (R(4) * p1) * T2 - R(3) * m / (R(4) * p2) * T3;
+  }
+  if (have2) return Tw + (T2 - Tw) * m / (R(2) * (R(1) + q));
+  return Tw;
+}
+
 // T at a node from its post-collision thermal deviations: T = T0 + sum h* - Q/2,
 // Q including the node's stored viscous source when that is enabled.
 template <typename S, typename R>
@@ -452,7 +501,38 @@ __device__ __forceinline__ void fixup(const DevGeom& g, const Co<R>& c, const S*
     if (MASK) wall = wall || ((fl >> (j - 1)) & 1u);
     if (wall) {
       const int i = opp_of(j);
-      d[j] = to_r(src[i * plane + own]);  // half-way bounce-back
+      // listed link of a masked lattice: its slot and wall fraction (1/2 otherwise)
+      int slot = -1;
+      R q = R(0.5);
+      if (MASK && !boxwall && (fl & kFlagLinks)) {
+        slot = g.slot[own];
+        q = (R)g.lk_q[8 * slot + (i - 1)];
+      }
+      // second node x_f - e_i = x + e_j, away from the wall
+      int x2 = x + ex, y2 = y + ey;
+      bool have2 = true;
+      if (x2 < 0 || x2 >= g.nx) {
+        if (g.px)
+          x2 = x2 < 0 ? x2 + g.nx : x2 - g.nx;
+        else
+          have2 = false;
+      }
+      if (y2 < 0 || y2 >= g.ny) {
+        if (g.py)
+          y2 = y2 < 0 ? y2 + g.ny : y2 - g.ny;
+        else
+          have2 = false;
+      }
+      const long long i2 = (long long)y2 * g.pitch + x2;
+      if (MASK && have2) have2 = (g.flags[i2] & kFlagSolid) == 0;
+      const R fi = to_r(src[i * plane + own]);
+      if (q == R(0.5) || (q < R(0.5) && !have2)) {
+        d[j] = fi;  // half-way bounce-back
+      } else if (q < R(0.5)) {  // f_i* interpolated to the point 1 - 2q behind x_f
+        d[j] = R(2) * q * fi + (R(1) - R(2) * q) * to_r(src[i * plane + i2]);
+      } else {  // the reflected value, 2q - 1 beyond x_f, interpolated with f_j* at x_f
+        d[j] = fi / (R(2) * q) + (R(2) * q - R(1)) / (R(2) * q) * to_r(src[j * plane + own]);
+      }
       if (j <= 4) {
         R ne, b1, b2, b3;
         if (boxwall) {
@@ -468,33 +548,44 @@ __device__ __forceinline__ void fixup(const DevGeom& g, const Co<R>& c, const S*
             b3 = (R)g.side_b[sd][2];
           }
         } else {
-          const int s = g.slot[own];
+          const int s = slot >= 0 ? slot : g.slot[own];
           const int t = g.lk_tbc[4 * s + (i - 1)];
           ne = (R)g.lk_ne[4 * s + (i - 1)];
           b1 = (R)g.tbc[3 * t + 0];
           b2 = (R)g.tbc[3 * t + 1];
           b3 = (R)g.tbc[3 * t + 2];
         }
-        // second node x_f - e_i = x + e_j, away from the wall
-        int x2 = x + ex, y2 = y + ey;
-        bool have2 = true;
-        if (x2 < 0 || x2 >= g.nx) {
-          if (g.px)
-            x2 = x2 < 0 ? x2 + g.nx : x2 - g.nx;
-          else
-            have2 = false;
-        }
-        if (y2 < 0 || y2 >= g.ny) {
-          if (g.py)
-            y2 = y2 < 0 ? y2 + g.ny : y2 - g.ny;
-          else
-            have2 = false;
-        }
-        const long long i2 = (long long)y2 * g.pitch + x2;
-        if (MASK && have2) have2 = (g.flags[i2] & kFlagSolid) == 0;
         const R T2 = have2 ? node_T(src, plane, i2, c) : R(0);
-        const R Tw = wall_temperature(b1, b2, b3, ne, T1, T2, have2);
-        h[j] = -to_r(src[(9 + i) * plane + own]) + c.cT2 * (Tw - c.T0);  // Eq. 26
+        R Tm;
+        if (q == R(0.5)) {
+          Tm = wall_temperature(b1, b2, b3, ne, T1, T2, have2);  // Eq. 28
+        } else {
+          const R Tw = wall_temperature_q(b1, b2, b3, ne, q, T1, T2, have2);
+          const bool dirichlet = b1 == R(0);
+          bool have3 = false;
+          R T3 = R(0);
+          if (q < R(0.5) && dirichlet && have2) {  // third node x + 2 e_j
+            int x3 = x2 + ex, y3 = y2 + ey;
+            have3 = true;
+            if (x3 < 0 || x3 >= g.nx) {
+              if (g.px)
+                x3 = x3 < 0 ? x3 + g.nx : x3 - g.nx;
+              else
+                have3 = false;
+            }
+            if (y3 < 0 || y3 >= g.ny) {
+              if (g.py)
+                y3 = y3 < 0 ? y3 + g.ny : y3 - g.ny;
+              else
+                have3 = false;
+            }
+            const long long i3 = (long long)y3 * g.pitch + x3;
+            if (MASK && have3) have3 = (g.flags[i3] & kFlagSolid) == 0;
+            if (have3) T3 = node_T(src, plane, i3, c);
+          }
+          Tm = midpoint_temperature_q(q, Tw, T1, T2, have2, T3, have3, dirichlet);
+        }
+        h[j] = -to_r(src[(9 + i) * plane + own]) + c.cT2 * (Tm - c.T0);  // Eq. 26
       }
     } else if (outx || outy) {  // periodic seam
       if (outx) sx = sx < 0 ? sx + g.nx : sx - g.nx;
@@ -922,9 +1013,15 @@ __global__ void __launch_bounds__(kRedThreads)
     const double T1 = node_T(b, g.plane, L.own, cd);
     const bool have2 = L.second >= 0;
     const double T2 = have2 ? node_T(b, g.plane, L.second, cd) : 0.0;
-    const double Tw = wall_temperature(L.b1, L.b2, L.b3, L.ne, T1, T2, have2);
-    const double grad = have2 ? (8.0 * Tw - 9.0 * T1 + T2) / (3.0 * L.ne)  // Eq. 27
-                              : (Tw - T1) / (0.5 * L.ne);
+    double grad;
+    if (L.q == 0.5) {
+      const double Tw = wall_temperature(L.b1, L.b2, L.b3, L.ne, T1, T2, have2);
+      grad = have2 ? (8.0 * Tw - 9.0 * T1 + T2) / (3.0 * L.ne)  // Eq. 27
+                   : (Tw - T1) / (0.5 * L.ne);
+    } else {  // wall off the link midpoint
+      const double Tw = wall_temperature_q(L.b1, L.b2, L.b3, L.ne, L.q, T1, T2, have2);
+      grad = wall_gradient_q(L.ne, L.q, Tw, T1, T2, have2);
+    }
     acc[0] += grad;
     acc[1] += isfinite(grad) ? 0.0 : 1.0;
   }

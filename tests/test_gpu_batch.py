@@ -88,3 +88,19 @@ def test_batch_flags_diverged_lattice():
     assert conv[1] == -1 and np.isfinite(res[1]) and res[1] < 1.0
     assert steps == 400
     b.close()
+
+
+def test_batch_with_walls_off_the_link_midpoint():
+    """Lattices with interpolated walls inside a batch reproduce their own
+    single-lattice runs."""
+    ws = [I.annulus(48, 2.6, Ra=1e4, interpolated=True),
+          I.offset_channel(12, 0.3, 0.8, 0.1, 0.1, 1e-5, top_tbc=(1.0, 0.2, 0.0), Q=1e-3),
+          I.natural_convection_cavity(24, 1e4)]
+    b = clbm.Batch(ws, "f64", autotune=False)
+    b.solve(0.0, 200, check_every=100)
+    for i, w in enumerate(ws):
+        s = clbm.from_workload(w, "f64")
+        s.step(200)
+        errs = compare(w, b.moments(i), s.moments())
+        assert max(errs.values()) <= 1e-13, (w.name, errs)
+    b.close()

@@ -211,3 +211,53 @@ def test_viscous_heating_channel_profile_gpu():
     o = oracle.from_workload(I.dissipation_channel(L, nu, alpha, Fx, nx=1))
     o.step(int(20 * L * L / alpha) + 2000)
     np.testing.assert_allclose(T[:, 0], o.moments()[3][:, 0], rtol=1e-10, atol=1e-18)
+
+
+def _offset_channel_convective():
+    """Walls at fractions 0.3 / 0.8 of a link, Robin top wall, heat source,
+    body force (peak velocity ~0.02, so FP32 rounding of the state stays well
+    below the tolerance): every off-midpoint rule is active."""
+    return I.offset_channel(12, 0.3, 0.8, 0.1, 0.1, 1e-4, top_tbc=(1.0, 0.2, 0.0), Q=1e-3)
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+@pytest.mark.parametrize("name", ["annulus", "channel", "channel_small_q"])
+def test_walls_off_the_link_midpoint_match_oracle(precision, name):
+    """Interpolated walls (no counterpart in the paper): the curved annulus with
+    every link's crossing fraction (diagonals included, convection on), and
+    offset channels, against the oracle."""
+    if name == "annulus":
+        w, steps = I.annulus(64, 2.6, Ra=1e4, interpolated=True), 400
+    elif name == "channel":
+        w, steps = _offset_channel_convective(), 3000
+    else:  # Dirichlet walls close to the nodes: the far-node extrapolation
+        w, steps = I.offset_channel(10, 0.05, 0.1, 0.1, 0.1, 1e-4, Q=1e-3), 3000
+    errs, (s, o) = run_pair(w, steps, precision)
+    _assert_within(errs, TOL[precision], f"{name} {precision}")
+    which = 4 if name == "annulus" else 5
+    a, b = s.nusselt(which, w.length, 1.0), o.nusselt(which, w.length, 1.0)
+    assert abs(a - b) <= (1e-11 if precision == "f64" else 1e-4) * max(1.0, abs(b))
+
+
+def test_offset_channel_steady_temperature_gpu():
+    """The steady parabola between offset walls (Robin top, source) on the GPU
+    in FP64, to rounding, as in the oracle."""
+    nu, alpha = 0.1, 0.1
+    w = I.offset_channel(8, 0.3, 0.2, nu, alpha, 1e-5, top_tbc=(1.0, 0.2, 0.0), Q=1e-3)
+    s = clbm.from_workload(w, "f64")
+    s.step(int(40 * 81 / alpha) + 2000)
+    T = s.moments()[3][:, 0]
+    _, Ta = I.offset_channel_exact(w, nu, alpha)
+    assert np.abs(T[1:-1] - Ta[1:-1]).max() < 1e-11
+
+
+def test_half_fraction_links_are_the_half_way_walls_gpu():
+    """Listing every link with q = 1/2 changes nothing, bit for bit."""
+    a = I.annulus(48, 2.6, Ra=1e4)
+    b = I.annulus(48, 2.6, Ra=1e4, interpolated=True)
+    b.geom.link_q = np.full(b.geom.n_links, 0.5)
+    sa, sb = clbm.from_workload(a, "f32"), clbm.from_workload(b, "f32")
+    sa.step(200)
+    sb.step(200)
+    for x, y in zip(sa.moments(), sb.moments()):
+        np.testing.assert_array_equal(x, y)
