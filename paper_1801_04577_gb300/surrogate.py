@@ -107,12 +107,18 @@ def make_net(G: int, base: int, levels: int, max_batch: int, seed: int = 7, stre
     return Net(G, IN_CH, OUT_CH, base, levels, max_batch, seed=seed, stream=stream, math=math)
 
 
-def train(net: Net, X, Y, M, epochs: int, batch: int, lr: float, seed: int = 11, log=None):
-    """Adam on minibatches of the torch CUDA tensors X [N,5,G,G], Y [N,3,G,G], M [N,G,G]."""
+def train(net: Net, X, Y, M, epochs: int, batch: int, lr: float, seed: int = 11, log=None,
+          lr_final: float = None):
+    """Adam on minibatches of the torch CUDA tensors X [N,5,G,G], Y [N,3,G,G], M [N,G,G];
+    the learning rate decays geometrically from lr to lr_final over the epochs
+    (constant when lr_final is None)."""
     import torch
     n = X.shape[0]
     losses = []
+    lr0 = lr
     for ep in range(epochs):
+        if lr_final is not None and epochs > 1:
+            lr = lr0 * (lr_final / lr0) ** (ep / (epochs - 1))
         perm = np.argsort(I.splitmix64_uniform(seed + ep, n))
         tot, cnt = 0.0, 0
         for s in range(0, n - batch + 1, batch):
