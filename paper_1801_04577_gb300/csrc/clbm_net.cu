@@ -277,6 +277,13 @@ struct TStoreAct {  // D(m = pixel, n = channel)
   StoreAct s;
   __device__ __forceinline__ void operator()(int m, int n, float v, int) const { s(n, m, v); }
 };
+struct TStoreSplit {  // D(m = pixel, n = channel) of split z -> part[z][n][m]
+  float* part;
+  int M, N;
+  __device__ __forceinline__ void operator()(int m, int n, float v, int z) const {
+    part[((long long)z * N + n) * M + m] = v;
+  }
+};
 struct TStorePartial {  // D(m = (ci, tap), n = co) of split z
   StorePartial s;
   __device__ __forceinline__ void operator()(int m, int n, float v, int z) const { s(n, m, v, z); }
@@ -378,6 +385,20 @@ __global__ void __launch_bounds__(GT) gemm_kernel(LA la, LB lb, ST st, int M, in
           st(m, n, acc[i][j]);
       }
     }
+}
+
+// Split-K forward / input-gradient GEMMs: D(pixel m, channel n) = sum over
+// splits of part[z][n][m] in order, then bias / ReLU / accumulation as the
+// unsplit epilogue would apply them.
+__global__ void splitk_finish_kernel(const float* __restrict__ part, int splits, int M, int N, StoreAct st) {
+  const long long tot = (long long)M * N;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int n = (int)(i / M), m = (int)(i - (long long)n * M);
+    float v = 0.0f;
+    for (int z = 0; z < splits; ++z) v += part[((long long)z * N + n) * M + m];
+    st(n, m, v);
+  }
 }
 
 // out[i] = sum_s part[s][i] (fixed order); optional accumulate
@@ -640,6 +661,35 @@ cudaError_t tc_gemm(clbm_net* net, GA ga, GB gb, ST st, int M, int N, int K, int
   return cudaGetLastError();
 }
 
+// K ranges of a forward / input-gradient GEMM: with fewer than two CTAs per
+// SM and at least eight 64-wide K slices, K is split (at least four slices per
+// range) until there are about two CTAs per SM.
+int conv_splits(int M, int N, int K) {
+  const int bn = tc::tile_n(N);
+  const long long ctas = (long long)((M + tc::kBM - 1) / tc::kBM) * ((N + bn - 1) / bn);
+  const int slices = (K + tc::kBK - 1) / tc::kBK;
+  if (ctas >= 2 * 152 || slices < 8) return 1;
+  const long long s = std::min<long long>((2 * 152 + ctas - 1) / ctas, slices / 4);
+  if (s <= 1) return 1;
+  const int kper = (int)(((K + s - 1) / s + tc::kBK - 1) / tc::kBK) * tc::kBK;
+  return (K + kper - 1) / kper;
+}
+
+// Implicit-im2col forward or input-gradient GEMM; split GEMMs finish in
+// splitk_finish_kernel.
+template <int KS, class GB>
+cudaError_t tc_conv_gemm(clbm_net* net, Act x, GB gb, StoreAct st, int M, int N, int K) {
+  const int splits = conv_splits(M, N, K);
+  if (splits == 1) return tc_gemm(net, GatherIm2col<KS>{x}, gb, TStoreAct{st}, M, N, K, K);
+  if ((long long)splits * M * N > net->part_cap) return cudaErrorInvalidValue;
+  const int kper = (K + splits - 1) / splits;
+  const int kp = (kper + tc::kBK - 1) / tc::kBK * tc::kBK;
+  cudaError_t e = tc_gemm(net, GatherIm2col<KS>{x}, gb, TStoreSplit{net->part, M, N}, M, N, K, kp);
+  if (e) return e;
+  splitk_finish_kernel<<<grid1((long long)M * N), 256, 0, net->stream>>>(net->part, (K + kp - 1) / kp, M, N, st);
+  return cudaGetLastError();
+}
+
 // Refresh the packed weight tiles from the BF16 weights (one launch, all layers).
 cudaError_t pack_weights(clbm_net* net) {
   if (!tensor_math(net)) return cudaSuccess;
@@ -674,8 +724,8 @@ cudaError_t conv_forward(clbm_net* net, const Conv& cv, Act x, int out_id, int o
   StoreAct st{net->act[out_id], net->act_c[out_id], out_coff, cv.H, cv.W, net->p + cv.b_off, relu, 0};
   if (tensor_math(net)) {  // D(pixel, co) = sum_k im2col(x)(pixel, k) W(co, k)
     const tc::Packed w = packed_of(net, cv.index, 0);
-    if (cv.ks == 3) return tc_gemm(net, GatherIm2col<3>{x}, w, TStoreAct{st}, Np, M, Kd, Kd);
-    return tc_gemm(net, GatherIm2col<1>{x}, w, TStoreAct{st}, Np, M, Kd, Kd);
+    if (cv.ks == 3) return tc_conv_gemm<3>(net, x, w, st, Np, M, Kd);
+    return tc_conv_gemm<1>(net, x, w, st, Np, M, Kd);
   }
   dim3 grid((Np + BN - 1) / BN, (M + BM - 1) / BM, 1);
   gemm_kernel<<<grid, GT, 0, net->stream>>>(la, lb, st, M, Np, Kd, Kd);
@@ -720,8 +770,8 @@ cudaError_t conv_backward(clbm_net* net, const Conv& cv, Act x, Act gy, int gx_i
     if (tensor_math(net)) {  // D(pixel, ci) = sum_k im2col(gy)(pixel, k) W'(ci, k)
       const tc::Packed w = packed_of(net, cv.index, 1);
       const int K = cv.co * kk;
-      if (cv.ks == 3) return tc_gemm(net, GatherIm2col<3>{gy}, w, TStoreAct{st}, Np, cv.ci, K, K);
-      return tc_gemm(net, GatherIm2col<1>{gy}, w, TStoreAct{st}, Np, cv.ci, K, K);
+      if (cv.ks == 3) return tc_conv_gemm<3>(net, gy, w, st, Np, cv.ci, K);
+      return tc_conv_gemm<1>(net, gy, w, st, Np, cv.ci, K);
     }
     flip_kernel<<<grid1((long long)cv.co * cv.ci * kk), 256, 0, net->stream>>>(
         net->pb + cv.w_off, net->pt + cv.w_off, cv.co, cv.ci, cv.ks);
@@ -992,6 +1042,10 @@ clbm_status clbm_net_create(const clbm_net_config* cfg, uint64_t seed, void* str
       const long long kper = dw_kper(c.math == CLBM_NET_TENSOR, Np, Kd, cv.co);
       cap = std::max(cap, ((Np + kper - 1) / kper) * cv.co * Kd);
       cap = std::max(cap, ((Np + kBiasChunk - 1) / kBiasChunk) * cv.co);  // bias chunk sums
+      if (c.math == CLBM_NET_TENSOR) {  // split-K forward and input-gradient GEMMs
+        cap = std::max(cap, (long long)conv_splits((int)Np, cv.co, Kd) * Np * cv.co);
+        cap = std::max(cap, (long long)conv_splits((int)Np, cv.ci, cv.co * cv.ks * cv.ks) * Np * cv.ci);
+      }
     }
   }
   n->part_cap = cap;
