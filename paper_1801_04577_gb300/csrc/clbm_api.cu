@@ -50,6 +50,8 @@ struct clbm_ctx {
   double* d_lk_ne = nullptr;
   int32_t* d_lk_tbc = nullptr;
   double* d_lk_q = nullptr;
+  uint8_t* d_tile_fluid = nullptr;  // masked lattices: which interior warp tiles hold fluid
+  int tiles_per_row = 0;
   double* d_tbc = nullptr;
   std::vector<int32_t> h_bnodes;  // nodes the boundary kernel recomputes (pitch layout)
   int32_t* d_bnodes = nullptr;
@@ -118,6 +120,9 @@ static DevGeom make_geom(const clbm_ctx* c) {
   g.lk_ne = c->d_lk_ne;
   g.lk_tbc = c->d_lk_tbc;
   g.lk_q = c->d_lk_q;
+  g.tile_fluid = c->d_tile_fluid;
+  g.tiles_per_row = c->tiles_per_row;
+  g.pad_tiles = 0;
   g.tbc = c->d_tbc;
   std::memcpy(g.side_b, c->side_b, sizeof(g.side_b));
   for (int sd = 0; sd < 4; ++sd)
@@ -153,6 +158,7 @@ static void free_tables(clbm_ctx* c) {
   cudaFree(c->d_lk_ne);
   cudaFree(c->d_lk_tbc);
   cudaFree(c->d_lk_q);
+  cudaFree(c->d_tile_fluid);
   cudaFree(c->d_tbc);
   cudaFree(c->d_bnodes);
   c->d_bnodes = nullptr;
@@ -161,6 +167,8 @@ static void free_tables(clbm_ctx* c) {
   c->d_lk_ne = nullptr;
   c->d_lk_tbc = nullptr;
   c->d_lk_q = nullptr;
+  c->d_tile_fluid = nullptr;
+  c->tiles_per_row = 0;
   c->d_tbc = nullptr;
   for (auto& kv : c->nu_lists) cudaFree(kv.second.first);
   c->nu_lists.clear();
@@ -439,6 +447,17 @@ clbm_status clbm_set_boundaries(clbm_ctx* c, const uint8_t* solid, const clbm_tb
       CLBM_CUDA(c, cudaMemcpy(c->d_lk_ne, lk_ne.data(), ns * sizeof(double), cudaMemcpyHostToDevice));
       CLBM_CUDA(c, cudaMemcpy(c->d_lk_tbc, lk_tbc.data(), ns * sizeof(int32_t), cudaMemcpyHostToDevice));
       CLBM_CUDA(c, cudaMemcpy(c->d_lk_q, lk_q.data(), 2 * ns * sizeof(double), cudaMemcpyHostToDevice));
+      if (!sol.empty()) {  // warp tiles of the interior kernel that hold no fluid node are skipped
+        const int tw = 32 * c->L->vec;
+        const int tpr = (nx + tw - 1) / tw;
+        std::vector<uint8_t> tf((size_t)ny * tpr, 0);
+        for (int y = 0; y < ny; ++y)
+          for (int x = 0; x < nx; ++x)
+            if (!sol[(size_t)y * nx + x]) tf[(size_t)y * tpr + x / tw] = 1;
+        CLBM_CUDA(c, cudaMalloc(&c->d_tile_fluid, tf.size()));
+        CLBM_CUDA(c, cudaMemcpy(c->d_tile_fluid, tf.data(), tf.size(), cudaMemcpyHostToDevice));
+        c->tiles_per_row = tpr;
+      }
     }
     {
       std::vector<double> t3((size_t)std::max(n_tbc, 1) * 3, 0.0);

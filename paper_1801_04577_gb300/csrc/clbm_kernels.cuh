@@ -792,8 +792,10 @@ __global__ void __launch_bounds__(kStepThreads) step_kernel(const StepArgs a) {
   const int warp = blockIdx.x * (kStepThreads / 32) + (threadIdx.x >> 5);
   const int xw = warp * 32 * V;
   if (xw >= a.g.nx) return;  // whole warps only: the shuffles need all 32 lanes
-  const Co<R> c = make_co<R>(a.c);
   const int y = a.reverse ? a.g.ny - 1 - (int)blockIdx.y : (int)blockIdx.y;
+  // a tile of solid nodes only: nothing reads them, so neither load nor store
+  if (a.g.tile_fluid && !a.g.tile_fluid[(long long)y * a.g.tiles_per_row + warp]) return;
+  const Co<R> c = make_co<R>(a.c);
   step_tile<S, V, false, VH, sizeof(S) != 2>(a.g, c, static_cast<const S*>(a.src),
                                              static_cast<S*>(a.dst), y, xw, lane, step_seed(a),
                                              a.stochastic);
