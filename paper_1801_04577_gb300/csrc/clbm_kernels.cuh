@@ -724,11 +724,16 @@ __device__ __forceinline__ void step_tile(const DevGeom& g, const Co<typename Tr
   }
   if constexpr (sizeof(S) == 2) {
     if (stochastic) {
+      // key: the full mixer of (step, node); per plane one multiply-xorshift of
+      // the key and a golden-ratio multiple of the plane, and one more for the
+      // second pair (the key already carries the entropy of step and node)
       const uint32_t key = seed ^ mix32((uint32_t)((long long)y * g.pitch + x0));
 #pragma unroll
       for (int q = 0; q < 14; ++q) {
-        const uint32_t r0 = mix32(key + 0x9E3779B9u * (uint32_t)(q + 1));
-        const uint32_t r1 = mix32(r0 ^ 0x85EBCA6Bu);
+        uint32_t r0 = (key ^ (0x9E3779B9u * (uint32_t)(q + 1))) * 0x7feb352du;
+        r0 ^= r0 >> 15;
+        uint32_t r1 = (r0 ^ 0x85EBCA6Bu) * 0x846ca68bu;
+        r1 ^= r1 >> 16;
         stv_sr<S, V>(out + q * plane, v[q], r0, r1);
       }
       return;
