@@ -104,3 +104,24 @@ def test_stochastic_rounding_beats_nearest_on_steady_cavity(cavity_ref):
         s.step(10000)
         err[rounding] = _l2(s.moments()[3], ref[3])
     assert err[1] < 0.1 * err[0]
+
+
+@pytest.mark.parametrize("precision,tol", [("f64", 1e-9), ("f32", 2e-2)])
+def test_rb_time_averaged_nusselt(precision, tol):
+    """Rayleigh-Benard 256 x 128 copy of the benchmark (Ra = 1e6): the bottom
+    wall's Nusselt number averaged over steps 10,000-20,000 (every 200 steps)
+    against the FP64 oracle.  FP64 reproduces it to rounding; FP32 to the
+    2 % that rounding differences can move a convection onset by."""
+    w = I.rayleigh_benard(256, 128)
+
+    def mean_nu(obj):
+        done, vals = 0, []
+        for t in range(10000, 20001, 200):
+            obj.step(t - done)
+            done = t
+            vals.append(obj.nusselt(2, w.length, w.dT))
+        return float(np.mean(vals))
+
+    ref = mean_nu(oracle.from_workload(w))
+    got = mean_nu(clbm.from_workload(w, precision))
+    assert abs(got - ref) <= tol * abs(ref), (got, ref)
