@@ -174,9 +174,26 @@ def time_oracle(budget_s: float = 12.0, nx: int = 2048, ny: int = 1024):
         el = time.perf_counter() - t0
         if el >= budget_s or n >= 200:
             break
-    return {"value": nx * ny * n / el / 1e6, "unit": "MLUPS", "cores": cores, "kind": "oracle",
-            "sample": f"FP64 oracle, Rayleigh-Benard {nx}x{ny} (same parameters as the workload), "
-                      f"{n} steps after 1 warm-up step, {el:.1f} s"}
+    out = {"value": nx * ny * n / el / 1e6, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+           "sample": f"FP64 oracle, Rayleigh-Benard {nx}x{ny} (same parameters as the workload), "
+                     f"{n} steps after 1 warm-up step, {el:.1f} s"}
+    # the same program on one core, on a smaller sample of the workload (about 3 s)
+    import oracle
+    del o
+    w1, o1, _ = oracle_rb_sample(512, 256)
+    oracle.set_threads(1)
+    try:
+        o1.step(1)
+        t0, n1 = time.perf_counter(), 0
+        while n1 < 100 and time.perf_counter() - t0 < 3.0:
+            o1.step(1)
+            n1 += 1
+        el1 = time.perf_counter() - t0
+    finally:
+        oracle.set_threads(cores)
+    out["single_thread"] = {"value": 512 * 256 * n1 / el1 / 1e6, "unit": "MLUPS",
+                            "sample": f"512x256, {n1} steps, {el1:.1f} s, 1 thread"}
+    return out
 
 
 def run_reference(args):
