@@ -253,7 +253,9 @@ clbm_status clbm_batch_create(const clbm_batch_item* items, int32_t n, int32_t a
  * per-step change over the interval.  Comparing states an even number of
  * steps apart ignores the small period-2 oscillation that closed cavities can
  * sustain, which keeps the one-step quantity of clbm_residual above tight
- * tolerances.  The first check of a solve only takes the snapshot.  Each check_every block of steps is one replay of a
+ * tolerances.  Per-node values are formed in the collision's arithmetic
+ * (FP32 below FP64 storage) and summed in FP64.  The first check of a solve
+ * only takes the snapshot.  Each check_every block of steps is one replay of a
  * captured CUDA graph; converged lattices leave the device-side work list.
  * Outputs (host arrays of n, may be NULL): conv_steps[i] = step count at
  * which lattice i converged, -1 if it did not, -2 if it diverged (NaN/Inf);

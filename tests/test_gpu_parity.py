@@ -261,3 +261,21 @@ def test_half_fraction_links_are_the_half_way_walls_gpu():
     sb.step(200)
     for x, y in zip(sa.moments(), sb.moments()):
         np.testing.assert_array_equal(x, y)
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+@pytest.mark.parametrize("case", ["row", "column", "two_rows", "single_node"])
+def test_degenerate_lattices_match_oracle(precision, case):
+    """Degenerate shapes: one periodic row (every pull in y wraps onto the
+    node itself), one periodic column, a two-row walled channel (every node is
+    a boundary node, with both walls on each column) and a single node."""
+    if case == "row":
+        w = I.periodic_box(200, 1)
+    elif case == "column":
+        w = I.periodic_box(1, 77)
+    elif case == "two_rows":
+        w = I.poiseuille_channel(2, 0.1, 1e-4, nx=9)
+    else:
+        w = I.periodic_box(1, 1)
+    errs, _ = run_pair(w, 150, precision)
+    _assert_within(errs, TOL[precision], f"{case} {precision}")
