@@ -191,16 +191,33 @@ __device__ __forceinline__ uint32_t cvt_rs2<__nv_bfloat16>(float lo, float hi, u
 
 // Stochastically rounded store of V values (16-bit formats only).
 template <typename S, int V>
-__device__ __forceinline__ void stv_sr(S* p, const float (&o)[V], uint32_t r0, uint32_t r1) {
+__device__ __forceinline__ void stv_sr(S* p, const float (&o)[V], uint32_t r0, uint32_t r1, int sub) {
   static_assert(sizeof(S) == 2, "stochastic rounding applies to 16-bit storage");
   if constexpr (V == 1) {
-    *reinterpret_cast<unsigned short*>(p) = (unsigned short)(cvt_rs2<S>(o[0], 0.0f, r0) & 0xFFFFu);
+    const uint32_t w = (sub & 2) ? r1 : r0;
+    *reinterpret_cast<unsigned short*>(p) =
+        (sub & 1) ? (unsigned short)(cvt_rs2<S>(0.0f, o[0], w) >> 16) : (unsigned short)(cvt_rs2<S>(o[0], 0.0f, w) & 0xFFFFu);
   } else if constexpr (V == 2) {
-    *reinterpret_cast<unsigned int*>(p) = cvt_rs2<S>(o[0], o[1], r0);
+    *reinterpret_cast<unsigned int*>(p) = cvt_rs2<S>(o[0], o[1], (sub & 2) ? r1 : r0);
   } else {
     static_assert(V == 4, "16-bit tiles use 1, 2 or 4 nodes per lane");
     *reinterpret_cast<uint2*>(p) = make_uint2(cvt_rs2<S>(o[0], o[1], r0), cvt_rs2<S>(o[2], o[3], r1));
   }
+}
+
+// The random bits of a store depend on the step, the node and the plane only,
+// whichever kernel updates the node: one key per group of four nodes x0 = x & ~3
+// of a row (the full mixer of step and node), and per plane two words from one
+// multiply-xorshift of the key and a golden-ratio multiple of the plane, and one
+// more; word 0 rounds nodes x0, x0 + 1 (low, high half), word 1 nodes x0 + 2, x0 + 3.
+__device__ __forceinline__ uint32_t sr_key(uint32_t seed, long long group_node) {
+  return seed ^ mix32((uint32_t)group_node);
+}
+__device__ __forceinline__ void sr_words(uint32_t key, int q, uint32_t& r0, uint32_t& r1) {
+  r0 = (key ^ (0x9E3779B9u * (uint32_t)(q + 1))) * 0x7feb352du;
+  r0 ^= r0 >> 15;
+  r1 = (r0 ^ 0x85EBCA6Bu) * 0x846ca68bu;
+  r1 ^= r1 >> 16;
 }
 
 // ---------------------------------------------------------------------------
@@ -602,10 +619,13 @@ __device__ __forceinline__ void fixup(const DevGeom& g, const Co<R>& c, const S*
 // ---------------------------------------------------------------------------
 // Store of one value (stochastically rounded for 16-bit storage when asked).
 template <typename S, typename R>
-__device__ __forceinline__ void st1(S* p, R v, int stochastic, uint32_t r) {
+__device__ __forceinline__ void st1(S* p, R v, int stochastic, uint32_t key, int q, int sub) {
   if constexpr (sizeof(S) == 2) {
     if (stochastic) {
-      *reinterpret_cast<unsigned short*>(p) = (unsigned short)(cvt_rs2<S>(v, 0.0f, r) & 0xFFFFu);
+      uint32_t r0, r1;
+      sr_words(key, q, r0, r1);
+      const float o[1] = {v};
+      stv_sr<S, 1>(p, o, r0, r1, sub);
       return;
     }
   }
@@ -709,32 +729,26 @@ __device__ __forceinline__ void step_tile(const DevGeom& g, const Co<typename Tr
   if constexpr (SKIP_EDGES) {
     // leave the first and last column to the boundary update running alongside
     if (x0 == 0 || (x0 <= g.nx - 1 && g.nx - 1 < x0 + V)) {
-      const uint32_t key = seed ^ mix32((uint32_t)((long long)y * g.pitch + x0));
 #pragma unroll
       for (int k = 0; k < V; ++k) {
         const int x = x0 + k;
         if (x == 0 || x == g.nx - 1) continue;
+        const uint32_t key = sr_key(seed, (long long)y * g.pitch + (x & ~3));
 #pragma unroll
-        for (int q = 0; q < 14; ++q)
-          st1<S, R>(out + q * plane + k, v[q][k], stochastic,
-                    mix32(key + 0x9E3779B9u * (uint32_t)(q + 1) + 0x632BE5ABu * (uint32_t)k));
+        for (int q = 0; q < 14; ++q) st1<S, R>(out + q * plane + k, v[q][k], stochastic, key, q, x & 3);
       }
       return;
     }
   }
   if constexpr (sizeof(S) == 2) {
     if (stochastic) {
-      // key: the full mixer of (step, node); per plane one multiply-xorshift of
-      // the key and a golden-ratio multiple of the plane, and one more for the
-      // second pair (the key already carries the entropy of step and node)
-      const uint32_t key = seed ^ mix32((uint32_t)((long long)y * g.pitch + x0));
+      // x0 is a multiple of V (tiles start at multiples of 32 V nodes)
+      const uint32_t key = sr_key(seed, (long long)y * g.pitch + (x0 & ~3));
 #pragma unroll
       for (int q = 0; q < 14; ++q) {
-        uint32_t r0 = (key ^ (0x9E3779B9u * (uint32_t)(q + 1))) * 0x7feb352du;
-        r0 ^= r0 >> 15;
-        uint32_t r1 = (r0 ^ 0x85EBCA6Bu) * 0x846ca68bu;
-        r1 ^= r1 >> 16;
-        stv_sr<S, V>(out + q * plane, v[q], r0, r1);
+        uint32_t r0, r1;
+        sr_words(key, q, r0, r1);
+        stv_sr<S, V>(out + q * plane, v[q], r0, r1, x0 & 3);
       }
       return;
     }
@@ -771,12 +785,9 @@ __device__ __forceinline__ void step_node(const DevGeom& g, const Co<typename Tr
   const bool vh = c.vhc != R(0);
   collide_any(c, vh, d, h, qv);
   if (vh) dst[14 * plane + i] = from_r<S, R>(qv);
-  const uint32_t key = seed ^ mix32((uint32_t)i);
+  const uint32_t key = sr_key(seed, i - (x & 3));  // the pitch is a multiple of 4
 #pragma unroll
-  for (int q = 0; q < 14; ++q) {
-    const uint32_t r = mix32(key + 0x9E3779B9u * (uint32_t)(q + 1));
-    st1<S, R>(dst + q * plane + i, q < 9 ? d[q] : h[q - 9], stochastic, r);
-  }
+  for (int q = 0; q < 14; ++q) st1<S, R>(dst + q * plane + i, q < 9 ? d[q] : h[q - 9], stochastic, key, q, x & 3);
 }
 
 // Stochastic-rounding key of a step: from the host value, or from the device

@@ -391,25 +391,45 @@ __global__ void __launch_bounds__(GT) gemm_kernel(LA la, LB lb, ST st, int M, in
 // splits of part[z][n][m] in order, then bias / ReLU / accumulation as the
 // unsplit epilogue would apply them.
 __global__ void splitk_finish_kernel(const float* __restrict__ part, int splits, int M, int N, StoreAct st) {
-  const long long tot = (long long)M * N;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot;
-       i += (long long)gridDim.x * blockDim.x) {
-    const int n = (int)(i / M), m = (int)(i - (long long)n * M);
-    float v = 0.0f;
-    for (int z = 0; z < splits; ++z) v += part[((long long)z * N + n) * M + m];
-    st(n, m, v);
+  for (int n = blockIdx.y; n < N; n += gridDim.y)
+    for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < M; m += gridDim.x * blockDim.x) {
+      float v = 0.0f;
+      for (int z = 0; z < splits; ++z) v += part[((long long)z * N + n) * M + m];
+      st(n, m, v);
+    }
+}
+
+// out[i] = sum_s part[s][i] in a fixed order. Block (32 x R) owns 32 outputs;
+// thread row r adds splits r, r + R, ... in turn, then the R row sums are
+// combined by a fixed pairwise tree, so many loads are in flight even when
+// there are few outputs and many splits.
+constexpr int kSumRows = 32;
+__global__ void sum_splits_kernel(const float* __restrict__ part, int splits, long long n,
+                                  float* __restrict__ out) {
+  __shared__ float sh[kSumRows][33];
+  const int R = blockDim.y, r = threadIdx.y, l = threadIdx.x;
+  for (long long i0 = (long long)blockIdx.x * 32; i0 < n; i0 += (long long)gridDim.x * 32) {
+    const long long i = i0 + l;
+    float s = 0.0f;
+    if (i < n)
+      for (int k = r; k < splits; k += R) s += part[(long long)k * n + i];
+    sh[r][l] = s;
+    __syncthreads();
+    for (int o = R / 2; o > 0; o >>= 1) {
+      if (r < o) sh[r][l] += sh[r + o][l];
+      __syncthreads();
+    }
+    if (r == 0 && i < n) out[i] = sh[0][l];
+    __syncthreads();
   }
 }
 
-// out[i] = sum_s part[s][i] (fixed order); optional accumulate
-__global__ void sum_splits_kernel(const float* __restrict__ part, int splits, long long n,
-                                  float* __restrict__ out) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-       i += (long long)gridDim.x * blockDim.x) {
-    float s = 0.0f;
-    for (int k = 0; k < splits; ++k) s += part[(long long)k * n + i];
-    out[i] = s;
-  }
+// launch shape of sum_splits_kernel: R = largest power of two <= min(splits, 32)
+void sum_splits(const float* part, int splits, long long n, float* out, cudaStream_t s) {
+  int R = 1;
+  while (2 * R <= std::min(splits, kSumRows)) R *= 2;
+  const long long blocks = std::min<long long>((n + 31) / 32, 65535);
+  sum_splits_kernel<<<(unsigned)std::max<long long>(blocks, 1), dim3(32, R), 0, s>>>(part, splits, n, out);
 }
 
 // Bias gradient db[c] = sum over samples and pixels of g[n][c][p], in two
@@ -422,11 +442,11 @@ __global__ void bias_partial_kernel(Act g, int N, float* __restrict__ part) {
   __shared__ float sh[GT];
   const int s = blockIdx.x, c = blockIdx.y;
   const int hw = g.H * g.W;
-  const long long tot = (long long)N * hw;
-  const long long k0 = (long long)s * kBiasChunk, k1 = min(tot, k0 + kBiasChunk);
+  const int tot = N * hw;  // below 2^31 (checked at network creation)
+  const int k0 = s * kBiasChunk, k1 = min(tot, k0 + kBiasChunk);
   float acc = 0.0f;
-  for (long long k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
-    const int nb = (int)(k / hw), p = (int)(k - (long long)nb * hw);
+  for (int k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
+    const int nb = k / hw, p = k - nb * hw;
     acc += g.base[((long long)nb * g.cs + g.coff + c) * hw + p];
   }
   sh[threadIdx.x] = acc;
@@ -438,67 +458,77 @@ __global__ void bias_partial_kernel(Act g, int N, float* __restrict__ part) {
   if (threadIdx.x == 0) part[(long long)s * gridDim.y + c] = sh[0];
 }
 
+// Element-wise kernels over activation views, launched on a 2-D grid: blockIdx.y
+// walks the (sample, channel) planes, blockIdx.x / threadIdx.x the pixels of
+// a plane, so the only index division is one per plane (plane_grid).
+dim3 plane_grid(int pixels, long long planes) {
+  const int bx = std::max(1, std::min((pixels + 255) / 256, 64));
+  return dim3((unsigned)bx, (unsigned)std::max<long long>(1, std::min<long long>(planes, 65535)));
+}
+
 // g *= (y > 0) over one activation view (ReLU backward, in place on g)
 __global__ void relu_back_kernel(Act y, float* __restrict__ g, int gcs, int gcoff, int N) {
-  const long long hw = (long long)y.H * y.W, tot = (long long)N * y.C * hw;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot;
-       i += (long long)gridDim.x * blockDim.x) {
-    const int nb = (int)(i / (y.C * hw));
-    const long long r = i - (long long)nb * y.C * hw;
-    const int c = (int)(r / hw);
-    const long long p = r - (long long)c * hw;
-    const float yv = y.base[((long long)nb * y.cs + y.coff + c) * hw + p];
-    float* gp = g + ((long long)nb * gcs + gcoff + c) * hw + p;
-    if (!(yv > 0.0f)) *gp = 0.0f;
+  const int hw = y.H * y.W;
+  for (int pc = blockIdx.y; pc < N * y.C; pc += gridDim.y) {
+    const int nb = pc / y.C, c = pc - nb * y.C;
+    const float* yp = y.base + ((long long)nb * y.cs + y.coff + c) * hw;
+    float* gp = g + ((long long)nb * gcs + gcoff + c) * hw;
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < hw; p += gridDim.x * blockDim.x)
+      if (!(yp[p] > 0.0f)) gp[p] = 0.0f;
   }
 }
 
 // 2x2 average pool: out (H/2 x W/2) from in; backward adds g_out/4 to the four inputs
 __global__ void pool_kernel(Act in, float* __restrict__ out, int ocs, int ocoff, int N) {
-  const int Ho = in.H / 2, Wo = in.W / 2;
-  const long long tot = (long long)N * in.C * Ho * Wo;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot;
-       i += (long long)gridDim.x * blockDim.x) {
-    const int x = (int)(i % Wo), y = (int)((i / Wo) % Ho), c = (int)((i / ((long long)Wo * Ho)) % in.C);
-    const int nb = (int)(i / ((long long)Wo * Ho * in.C));
-    const float s = in.at(nb, c, 2 * y, 2 * x) + in.at(nb, c, 2 * y, 2 * x + 1) +
-                    in.at(nb, c, 2 * y + 1, 2 * x) + in.at(nb, c, 2 * y + 1, 2 * x + 1);
-    out[((long long)nb * ocs + ocoff + c) * Ho * Wo + (long long)y * Wo + x] = 0.25f * s;
+  const int Wo = in.W / 2, ho = (in.H / 2) * Wo, hw = in.H * in.W;
+  for (int pc = blockIdx.y; pc < N * in.C; pc += gridDim.y) {
+    const int nb = pc / in.C, c = pc - nb * in.C;
+    const float* ip = in.base + ((long long)nb * in.cs + in.coff + c) * hw;
+    float* op = out + ((long long)nb * ocs + ocoff + c) * ho;
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < ho; p += gridDim.x * blockDim.x) {
+      const int y = p / Wo, x = p - y * Wo;
+      const float* q = ip + 2 * y * in.W + 2 * x;
+      op[p] = 0.25f * ((q[0] + q[1]) + (q[in.W] + q[in.W + 1]));
+    }
   }
 }
 __global__ void pool_back_kernel(Act gout, float* __restrict__ gin, int gcs, int gcoff, int N) {
-  const int H = gout.H * 2, W = gout.W * 2;
-  const long long tot = (long long)N * gout.C * H * W;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot;
-       i += (long long)gridDim.x * blockDim.x) {
-    const int x = (int)(i % W), y = (int)((i / W) % H), c = (int)((i / ((long long)W * H)) % gout.C);
-    const int nb = (int)(i / ((long long)W * H * gout.C));
-    gin[((long long)nb * gcs + gcoff + c) * H * W + (long long)y * W + x] +=
-        0.25f * gout.at(nb, c, y / 2, x / 2);
+  const int W = gout.W * 2, hw = gout.H * 2 * W, ho = gout.H * gout.W;
+  for (int pc = blockIdx.y; pc < N * gout.C; pc += gridDim.y) {
+    const int nb = pc / gout.C, c = pc - nb * gout.C;
+    const float* gp = gout.base + ((long long)nb * gout.cs + gout.coff + c) * ho;
+    float* ip = gin + ((long long)nb * gcs + gcoff + c) * hw;
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < hw; p += gridDim.x * blockDim.x) {
+      const int y = p / W, x = p - y * W;
+      ip[p] += 0.25f * gp[(y >> 1) * gout.W + (x >> 1)];
+    }
   }
 }
 
 // nearest 2x upsample; backward sums the four outputs of each input
 __global__ void up_kernel(Act in, float* __restrict__ out, int ocs, int ocoff, int N) {
-  const int H = in.H * 2, W = in.W * 2;
-  const long long tot = (long long)N * in.C * H * W;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot;
-       i += (long long)gridDim.x * blockDim.x) {
-    const int x = (int)(i % W), y = (int)((i / W) % H), c = (int)((i / ((long long)W * H)) % in.C);
-    const int nb = (int)(i / ((long long)W * H * in.C));
-    out[((long long)nb * ocs + ocoff + c) * H * W + (long long)y * W + x] = in.at(nb, c, y / 2, x / 2);
+  const int W = in.W * 2, hw = in.H * 2 * W, hi = in.H * in.W;
+  for (int pc = blockIdx.y; pc < N * in.C; pc += gridDim.y) {
+    const int nb = pc / in.C, c = pc - nb * in.C;
+    const float* ip = in.base + ((long long)nb * in.cs + in.coff + c) * hi;
+    float* op = out + ((long long)nb * ocs + ocoff + c) * hw;
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < hw; p += gridDim.x * blockDim.x) {
+      const int y = p / W, x = p - y * W;
+      op[p] = ip[(y >> 1) * in.W + (x >> 1)];
+    }
   }
 }
 __global__ void up_back_kernel(Act gout, float* __restrict__ gin, int gcs, int gcoff, int N) {
-  const int Hi = gout.H / 2, Wi = gout.W / 2;
-  const long long tot = (long long)N * gout.C * Hi * Wi;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot;
-       i += (long long)gridDim.x * blockDim.x) {
-    const int x = (int)(i % Wi), y = (int)((i / Wi) % Hi), c = (int)((i / ((long long)Wi * Hi)) % gout.C);
-    const int nb = (int)(i / ((long long)Wi * Hi * gout.C));
-    const float s = gout.at(nb, c, 2 * y, 2 * x) + gout.at(nb, c, 2 * y, 2 * x + 1) +
-                    gout.at(nb, c, 2 * y + 1, 2 * x) + gout.at(nb, c, 2 * y + 1, 2 * x + 1);
-    gin[((long long)nb * gcs + gcoff + c) * Hi * Wi + (long long)y * Wi + x] += s;
+  const int Wi = gout.W / 2, hi = (gout.H / 2) * Wi, hw = gout.H * gout.W;
+  for (int pc = blockIdx.y; pc < N * gout.C; pc += gridDim.y) {
+    const int nb = pc / gout.C, c = pc - nb * gout.C;
+    const float* gp = gout.base + ((long long)nb * gout.cs + gout.coff + c) * hw;
+    float* ip = gin + ((long long)nb * gcs + gcoff + c) * hi;
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < hi; p += gridDim.x * blockDim.x) {
+      const int y = p / Wi, x = p - y * Wi;
+      const float* q = gp + 2 * y * gout.W + 2 * x;
+      ip[p] += (q[0] + q[1]) + (q[gout.W] + q[gout.W + 1]);
+    }
   }
 }
 
@@ -686,7 +716,8 @@ cudaError_t tc_conv_gemm(clbm_net* net, Act x, GB gb, StoreAct st, int M, int N,
   const int kp = (kper + tc::kBK - 1) / tc::kBK * tc::kBK;
   cudaError_t e = tc_gemm(net, GatherIm2col<KS>{x}, gb, TStoreSplit{net->part, M, N}, M, N, K, kp);
   if (e) return e;
-  splitk_finish_kernel<<<grid1((long long)M * N), 256, 0, net->stream>>>(net->part, (K + kp - 1) / kp, M, N, st);
+  splitk_finish_kernel<<<dim3((unsigned)std::min((M + 255) / 256, 64), (unsigned)std::min(N, 65535)), 256, 0, net->stream>>>(
+      net->part, (K + kp - 1) / kp, M, N, st);
   return cudaGetLastError();
 }
 
@@ -757,12 +788,12 @@ cudaError_t conv_backward(clbm_net* net, const Conv& cv, Act x, Act gy, int gx_i
       gemm_kernel<<<grid, GT, 0, net->stream>>>(la, lb, st, cv.co, Kd, Np, kper);
     }
     const long long n = (long long)cv.co * Kd;
-    sum_splits_kernel<<<grid1(n), 256, 0, net->stream>>>(net->part, splits, n, net->g + cv.w_off);
+    sum_splits(net->part, splits, n, net->g + cv.w_off, net->stream);
     // bias: the split-K partials are consumed, so part holds the chunk sums next
     const int chunks = (Np + kBiasChunk - 1) / kBiasChunk;
     if ((long long)chunks * cv.co > net->part_cap) return cudaErrorInvalidValue;
     bias_partial_kernel<<<dim3(chunks, cv.co), GT, 0, net->stream>>>(gy, N, net->part);
-    sum_splits_kernel<<<grid1(cv.co), 256, 0, net->stream>>>(net->part, chunks, cv.co, net->g + cv.b_off);
+    sum_splits(net->part, chunks, cv.co, net->g + cv.b_off, net->stream);
   }
   if (gx_id >= 0) {  // input gradient: M = ci, N = pixels, K = co*t, with flipped weights
     const int kk = cv.ks * cv.ks;
@@ -785,7 +816,7 @@ cudaError_t conv_backward(clbm_net* net, const Conv& cv, Act x, Act gy, int gx_i
 
 cudaError_t relu_back(clbm_net* net, int id, int coff, int C, int N) {
   Act y = view(net, id, coff, C);
-  relu_back_kernel<<<grid1((long long)N * C * y.H * y.W), 256, 0, net->stream>>>(
+  relu_back_kernel<<<plane_grid(y.H * y.W, (long long)N * C), 256, 0, net->stream>>>(
       y, net->gact[id], net->act_c[id], coff, N);
   return cudaGetLastError();
 }
@@ -801,7 +832,7 @@ cudaError_t forward(clbm_net* net, const Plan& P, int N) {
     if ((e = conv_forward(net, net->convs[ci++], x, P.a1[l], 0, 1, N))) return e;
     if ((e = conv_forward(net, net->convs[ci++], view(net, P.a1[l], 0, c), P.cat[l], cup, 1, N))) return e;
     Act skip = view(net, P.cat[l], cup, c);
-    pool_kernel<<<grid1((long long)N * c * (skip.H / 2) * (skip.W / 2)), 256, 0, net->stream>>>(
+    pool_kernel<<<plane_grid((skip.H / 2) * (skip.W / 2), (long long)N * c), 256, 0, net->stream>>>(
         skip, net->act[P.pool[l]], c, 0, N);
     x = view(net, P.pool[l], 0, c);
   }
@@ -811,7 +842,7 @@ cudaError_t forward(clbm_net* net, const Plan& P, int N) {
   Act prev = view(net, P.b2, 0, cb);
   for (int l = L - 2; l >= 0; --l) {
     const int c = B << l, cup = B << (l + 1);
-    up_kernel<<<grid1((long long)N * cup * (prev.H * 2) * (prev.W * 2)), 256, 0, net->stream>>>(
+    up_kernel<<<plane_grid(prev.H * 2 * prev.W * 2, (long long)N * cup), 256, 0, net->stream>>>(
         prev, net->act[P.cat[l]], net->act_c[P.cat[l]], 0, N);
     if ((e = conv_forward(net, net->convs[ci++], view(net, P.cat[l], 0, cup + c), P.d1[l], 0, 1, N))) return e;
     if ((e = conv_forward(net, net->convs[ci++], view(net, P.d1[l], 0, c), P.d2[l], 0, 1, N))) return e;
@@ -849,7 +880,7 @@ cudaError_t backward(clbm_net* net, const Plan& P, int N) {
     // gradient of the upsampled part flows to the level below (d2[l+1] or b2)
     const int below = (l + 1 <= L - 2) ? P.d2[l + 1] : P.b2;
     Act gup = view(net, P.cat[l], 0, cup, true);
-    up_back_kernel<<<grid1((long long)N * cup * (gup.H / 2) * (gup.W / 2)), 256, 0, net->stream>>>(
+    up_back_kernel<<<plane_grid((gup.H / 2) * (gup.W / 2), (long long)N * cup), 256, 0, net->stream>>>(
         gup, net->gact[below], net->act_c[below], 0, N);
   }
   // bottleneck
@@ -871,7 +902,7 @@ cudaError_t backward(clbm_net* net, const Plan& P, int N) {
     const Conv& c1 = net->convs[ci--];
     // pool backward adds into the skip part of cat[l]
     Act gp = view(net, P.pool[l], 0, c, true);
-    pool_back_kernel<<<grid1((long long)N * c * gp.H * 2 * gp.W * 2), 256, 0, net->stream>>>(
+    pool_back_kernel<<<plane_grid(gp.H * 2 * gp.W * 2, (long long)N * c), 256, 0, net->stream>>>(
         gp, net->gact[P.cat[l]], net->act_c[P.cat[l]], cup, N);
     if ((e = relu_back(net, P.cat[l], cup, c, N))) return e;
     if ((e = conv_backward(net, c2, view(net, P.a1[l], 0, c), view(net, P.cat[l], cup, c, true), P.a1[l], 0, N))) return e;
@@ -942,7 +973,8 @@ clbm_status clbm_net_create(const clbm_net_config* cfg, uint64_t seed, void* str
   const clbm_net_config& c = *cfg;
   if (c.levels < 2 || c.levels > kMaxLevels || c.base < 1 || c.in_ch < 1 || c.out_ch < 1 ||
       c.max_batch < 1 || c.grid < 2 || (c.grid % (1 << (c.levels - 1))) != 0 ||
-      (c.math != CLBM_NET_TENSOR && c.math != CLBM_NET_FP32))
+      (c.math != CLBM_NET_TENSOR && c.math != CLBM_NET_FP32) ||
+      (long long)c.max_batch * c.grid * c.grid >= (1LL << 31))
     return CLBM_EINVAL;
   clbm_net* n = new (std::nothrow) clbm_net();
   if (!n) return CLBM_ENOMEM;

@@ -39,6 +39,25 @@ def test_batch_matches_single_lattice_runs(precision, autotune):
     b.close()
 
 
+@pytest.mark.parametrize("precision,rounding", [("bf16", 0), ("bf16", 1), ("f16", 0), ("f16", 1)])
+def test_batch_16bit_storage_matches_single_lattice_runs(precision, rounding):
+    """16-bit storage of deviations, FP32 collision, in the batch: every lattice
+    reproduces its own single-lattice run at the same storage format and
+    rounding mode (the stochastic-rounding bits depend on the step and the
+    lattice-local node only, so they are the same in both)."""
+    ws = mixed_workloads()
+    b = clbm.Batch(ws, precision, rounding=rounding)
+    conv, res, steps = b.solve(0.0, 200, check_every=100)
+    assert steps == 200 and (conv == -1).all()
+    for i, w in enumerate(ws):
+        s = clbm.from_workload(w, precision, rounding=rounding)
+        s.step(200)
+        errs = compare(w, b.moments(i), s.moments())
+        print(precision, rounding, w.name, errs)
+        assert max(errs.values()) <= 1e-6, (i, w.name, errs)
+    b.close()
+
+
 def test_batch_against_oracle_f64():
     ws = mixed_workloads()[:3]
     b = clbm.Batch(ws, "f64")

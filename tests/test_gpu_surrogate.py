@@ -163,7 +163,10 @@ def test_warm_start_reaches_steady_state_in_fewer_steps():
     M = X[:, 0].copy()
     net = SG.make_net(G, base=16, levels=3, max_batch=32, seed=9, stream=stream.cuda_stream)
     Xd, Yd, Md = (torch.from_numpy(a).cuda() for a in (X, Y, M))
-    losses = SG.train(net, Xd, Yd, Md, epochs=60, batch=32, lr=2e-3)
+    # the learning rate decays to 2e-4: at a constant 2e-3 the last epochs are
+    # noisy and the step saving swings between 10 % and 35 % with the rounding
+    # order of the gradient sums
+    losses = SG.train(net, Xd, Yd, Md, epochs=60, batch=32, lr=2e-3, lr_final=2e-4)
     assert losses[-1] < 0.2 * losses[0]
     test_ws = I.obstacle_cavities(32, G, seed=9001)
     r = SG.compare_starts(net, test_ws, tol, cap, stream=stream.cuda_stream)
