@@ -468,14 +468,15 @@ def conv_flops_per_train_step(G, cin, cout, base, levels, batch):
 
 
 def run_unet(args):
-    """Training steps of the warm-start U-Net (64^2 grid, widths 24..192,
-    1.1 M parameters, batch 32) on the tensor cores."""
+    """Training steps of the warm-start U-Net on the tensor cores (default: 64^2
+    grid, widths 24..192, 1.1 M parameters, batch 32; --net-grid 128 gives the
+    same network on 128^2 grids)."""
     import torch
 
     from paper_1801_04577_gb300.net import Net
     if not torch.cuda.is_available():
         raise SystemExit("bench.py: no CUDA device (the library has no CPU path)")
-    G, cin, cout, base, levels, B = 64, 5, 3, 24, 4, args.net_batch
+    G, cin, cout, base, levels, B = args.net_grid, 5, 3, args.net_base, args.net_levels, args.net_batch
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     net = Net(G, cin, cout, base, levels, B, seed=3, stream=stream.cuda_stream, math=args.net_math)
@@ -523,7 +524,7 @@ def run_unet(args):
             "config": {"workload": f"unet_g{G}_b{base}_l{levels}_batch{B}_{args.net_math}",
                        "parameters": net.nparam, "forward_ms": f0.elapsed_time(f1) / 20,
                        "conv_gflop_per_step": flops / 1e9, "loss_last": loss,
-                       "l2": "activations of one batch (~0.3 GB) larger than L2 in the first level"},
+                       "l2": f"activations of one batch (~{0.3 * (G / 64) ** 2:.1f} GB) larger than L2 in the first level"},
             "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": None,
                          "kernel": "tc::gemm_kernel (all convolution GEMMs of a training step)",
@@ -552,6 +553,9 @@ def main():
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--check-every", type=int, default=100)
     ap.add_argument("--net-batch", type=int, default=32)
+    ap.add_argument("--net-grid", type=int, default=64)
+    ap.add_argument("--net-base", type=int, default=24)
+    ap.add_argument("--net-levels", type=int, default=4)
     ap.add_argument("--net-math", choices=["tensor", "fp32"], default="tensor")
     args = ap.parse_args()
     if args.warmup < 3:
