@@ -447,13 +447,21 @@ clbm_status clbm_set_boundaries(clbm_ctx* c, const uint8_t* solid, const clbm_tb
       CLBM_CUDA(c, cudaMemcpy(c->d_lk_ne, lk_ne.data(), ns * sizeof(double), cudaMemcpyHostToDevice));
       CLBM_CUDA(c, cudaMemcpy(c->d_lk_tbc, lk_tbc.data(), ns * sizeof(int32_t), cudaMemcpyHostToDevice));
       CLBM_CUDA(c, cudaMemcpy(c->d_lk_q, lk_q.data(), 2 * ns * sizeof(double), cudaMemcpyHostToDevice));
-      if (!sol.empty()) {  // warp tiles of the interior kernel that hold no fluid node are skipped
+      {  // classes of the interior kernel's warp tiles (32 vec nodes of a row): 0 = no
+         // fluid node (skipped), 1 = fluid nodes only, none flagged, 2 = holds a
+         // flagged node (solid, or fluid next to a wall) whose store it leaves out
         const int tw = 32 * c->L->vec;
         const int tpr = (nx + tw - 1) / tw;
-        std::vector<uint8_t> tf((size_t)ny * tpr, 0);
+        std::vector<uint8_t> tf((size_t)ny * tpr, 0), flagged((size_t)ny * tpr, 0);
         for (int y = 0; y < ny; ++y)
-          for (int x = 0; x < nx; ++x)
-            if (!sol[(size_t)y * nx + x]) tf[(size_t)y * tpr + x / tw] = 1;
+          for (int x = 0; x < nx; ++x) {
+            const uint16_t f = flags[(size_t)y * c->pitch + x];
+            const size_t t = (size_t)y * tpr + x / tw;
+            if (!(f & kFlagSolid)) tf[t] = 1;
+            if (f) flagged[t] = 1;
+          }
+        for (size_t t = 0; t < tf.size(); ++t)
+          if (tf[t] && flagged[t]) tf[t] = 2;
         CLBM_CUDA(c, cudaMalloc(&c->d_tile_fluid, tf.size()));
         CLBM_CUDA(c, cudaMemcpy(c->d_tile_fluid, tf.data(), tf.size(), cudaMemcpyHostToDevice));
         c->tiles_per_row = tpr;

@@ -32,7 +32,8 @@ struct DevGeom {
   const int32_t* lk_tbc;       // [nslots][4] condition index, -1 = no link
   const double* lk_q;          // [nslots][8] wall fraction q per link direction i = 1..8 (0.5 = half-way)
   const double* tbc;           // [ntbc][3] (b1, b2, b3)
-  const uint8_t* tile_fluid;   // [ny][tiles_per_row]: 0 = warp tile (32 V nodes of a row) all solid, or nullptr
+  const uint8_t* tile_fluid;   // [ny][tiles_per_row] class of each warp tile (32 V nodes of a row): 0 = no
+                               // fluid node, 1 = no flagged node, 2 = holds flagged nodes; nullptr = box lattice
   int tiles_per_row, pad_tiles;
   double side_b[4][3];         // conditions of the box sides x0, x1, y0, y1
   float side_bf[4][3];         // the same rounded to FP32 (for FP32 arithmetic)

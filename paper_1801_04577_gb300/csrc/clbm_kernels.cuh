@@ -640,10 +640,12 @@ __device__ __forceinline__ void st1(S* p, R v, int stochastic, uint32_t key, int
 // next to solids come out wrong here and are recomputed afterwards by the
 // boundary kernel from its precomputed node list.  Keeping the walls out of
 // this kernel keeps its warps free of divergent wall code.
-template <typename S, int V, bool SKIP_EDGES = false, bool VH = false, bool SKIP_DEAD = true>
+template <typename S, int V, bool SKIP_EDGES = false, bool VH = false, bool SKIP_DEAD = true,
+          bool MASKSTORE = false>
 __device__ __forceinline__ void step_tile(const DevGeom& g, const Co<typename Traits<S>::R>& c,
                                           const S* __restrict__ src, S* __restrict__ dst, int y,
-                                          int xw, int lane, uint32_t seed, int stochastic) {
+                                          int xw, int lane, uint32_t seed, int stochastic,
+                                          bool mixed = false) {
   using R = typename Traits<S>::R;
   const int x0 = xw + lane * V;
   const long long plane = g.plane;
@@ -715,6 +717,31 @@ __device__ __forceinline__ void step_tile(const DevGeom& g, const Co<typename Tr
 
   if (!live) return;
   S* out = dst + (long long)y * g.pitch + x0;
+  if constexpr (MASKSTORE) {
+    // a tile holding flagged nodes (solid, or fluid next to a wall) leaves them,
+    // and the edge columns, to the boundary update of the same launch
+    if (mixed) {
+      const uint16_t* fp = g.flags + (long long)y * g.pitch + x0;
+      uint32_t skip = 0;
+#pragma unroll
+      for (int k = 0; k < V; ++k) {
+        const int x = x0 + k;
+        if (fp[k] != 0 || x == 0 || x == g.nx - 1) skip |= 1u << k;
+      }
+      if (skip) {
+#pragma unroll
+        for (int k = 0; k < V; ++k) {
+          if ((skip >> k) & 1u) continue;
+          const int x = x0 + k;
+          if constexpr (VH) out[14 * plane + k] = from_r<S, R>(qv[k]);
+          const uint32_t key = sr_key(seed, (long long)y * g.pitch + (x & ~3));
+#pragma unroll
+          for (int q = 0; q < 14; ++q) st1<S, R>(out + q * plane + k, v[q][k], stochastic, key, q, x & 3);
+        }
+        return;
+      }
+    }
+  }
   if constexpr (VH) {  // the viscous source of this step, read back with T (15th plane)
     if constexpr (SKIP_EDGES) {
 #pragma unroll
@@ -834,7 +861,7 @@ __global__ void __launch_bounds__(kRedThreads) boundary_kernel(const StepArgs a)
 // interior tiles of rows that are not boundary rows, which skip the first and
 // last column.  The latency-bound boundary work then overlaps the streaming
 // interior work instead of following it.
-template <typename S, bool VH>
+template <typename S, bool VH, bool MASKED = false>
 __global__ void __launch_bounds__(kStepThreads, 5) step_fused_kernel(const StepArgs a, int nbb,
                                                                   int xblocks, int y0) {
   using R = typename Traits<S>::R;
@@ -843,8 +870,8 @@ __global__ void __launch_bounds__(kStepThreads, 5) step_fused_kernel(const StepA
   if ((int)blockIdx.x < nbb) {
     const int k = blockIdx.x * kStepThreads + threadIdx.x;
     if (k < a.nb)
-      step_node<S, false>(a.g, c, static_cast<const S*>(a.src), static_cast<S*>(a.dst), a.bnodes[k],
-                          step_seed(a), a.stochastic);
+      step_node<S, MASKED>(a.g, c, static_cast<const S*>(a.src), static_cast<S*>(a.dst), a.bnodes[k],
+                           step_seed(a), a.stochastic);
     return;
   }
   const int b = blockIdx.x - nbb;
@@ -855,9 +882,17 @@ __global__ void __launch_bounds__(kStepThreads, 5) step_fused_kernel(const StepA
   const int warp = (b % xblocks) * (kStepThreads / 32) + (threadIdx.x >> 5);
   const int xw = warp * 32 * V;
   if (xw >= a.g.nx) return;  // whole warps only
-  step_tile<S, V, true, VH, sizeof(S) != 2>(a.g, c, static_cast<const S*>(a.src),
-                                            static_cast<S*>(a.dst), y, xw, lane, step_seed(a),
-                                            a.stochastic);
+  if constexpr (MASKED) {  // tile classes: 0 no fluid, 1 unflagged fluid, 2 holds flagged nodes
+    const uint8_t cls = a.g.tile_fluid[(long long)y * a.g.tiles_per_row + warp];
+    if (!cls) return;
+    step_tile<S, V, true, VH, sizeof(S) != 2, true>(a.g, c, static_cast<const S*>(a.src),
+                                                    static_cast<S*>(a.dst), y, xw, lane, step_seed(a),
+                                                    a.stochastic, cls == 2);
+  } else {
+    step_tile<S, V, true, VH, sizeof(S) != 2>(a.g, c, static_cast<const S*>(a.src),
+                                              static_cast<S*>(a.dst), y, xw, lane, step_seed(a),
+                                              a.stochastic);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -1229,16 +1264,27 @@ struct LaunchImpl {
   static cudaError_t step(const StepArgs& a, cudaStream_t s) {
     const int nodes_per_block = kStepThreads * V;
     const int xblocks = (a.g.nx + nodes_per_block - 1) / nodes_per_block;
-    if (!a.g.flags) {  // box lattice: one fused launch
+    // one fused launch: boundary nodes in the first blocks, interior tiles in the
+    // rest (box lattices; masked ones with their tile classes, whose interior
+    // tiles leave the listed nodes out)
+    if (!a.g.flags || a.g.tile_fluid) {
       const int y0 = a.g.py ? 0 : 1;
       const int rows = a.g.py ? a.g.ny : (a.g.ny > 2 ? a.g.ny - 2 : 0);
       const int nbb = (a.nb + kStepThreads - 1) / kStepThreads;
       const long long blocks = (long long)nbb + (long long)xblocks * rows;
       if (blocks > 0 && blocks < (1LL << 31)) {
-        if (a.c.vh)
-          step_fused_kernel<S, true><<<(unsigned)blocks, kStepThreads, 0, s>>>(a, nbb, xblocks, y0);
-        else
-          step_fused_kernel<S, false><<<(unsigned)blocks, kStepThreads, 0, s>>>(a, nbb, xblocks, y0);
+        const unsigned nblk = (unsigned)blocks;
+        if (a.g.flags) {
+          if (a.c.vh)
+            step_fused_kernel<S, true, true><<<nblk, kStepThreads, 0, s>>>(a, nbb, xblocks, y0);
+          else
+            step_fused_kernel<S, false, true><<<nblk, kStepThreads, 0, s>>>(a, nbb, xblocks, y0);
+        } else {
+          if (a.c.vh)
+            step_fused_kernel<S, true><<<nblk, kStepThreads, 0, s>>>(a, nbb, xblocks, y0);
+          else
+            step_fused_kernel<S, false><<<nblk, kStepThreads, 0, s>>>(a, nbb, xblocks, y0);
+        }
         return cudaGetLastError();
       }
     }
