@@ -6,6 +6,8 @@ density as rho - rho0 relative to rho0).  Cases cover several warp tiles, ragged
 row lengths, both kinds of walls, periodic seams, masks with listed links,
 curved walls, the heat source and the body force.
 """
+import copy
+
 import numpy as np
 import pytest
 
@@ -279,3 +281,29 @@ def test_degenerate_lattices_match_oracle(precision, case):
         w = I.periodic_box(1, 1)
     errs, _ = run_pair(w, 150, precision)
     _assert_within(errs, TOL[precision], f"{case} {precision}")
+
+
+@pytest.mark.parametrize("precision,rounding", [("f64", 0), ("f32", 0), ("bf16", 1)])
+@pytest.mark.parametrize("name", ["cavity", "rb_periodic_x", "periodic_box", "viscous"])
+def test_all_fluid_mask_is_bit_identical_to_the_box(precision, rounding, name):
+    """A mask with no solid node makes the lattice 'masked': flags, the three-class
+    tile table, and the fused launch whose flagged tiles store node by node and
+    leave the listed nodes to the boundary blocks.  The walls are the same, so
+    every value must equal the unmasked run's bit for bit."""
+    if name == "cavity":
+        w = I.natural_convection_cavity(150, 1e4)
+    elif name == "rb_periodic_x":
+        w = I.rayleigh_benard(300, 70, Ra=1e5, Q=1e-4, noise=1e-2)
+    elif name == "periodic_box":
+        w = I.periodic_box(133, 37)
+    else:  # the viscous dissipation source (a 15th plane stored by the tiles)
+        w = I.natural_convection_cavity(70, 1e5)
+        w.params.viscous_heating = 1
+    m = copy.deepcopy(w)
+    m.geom.solid = np.zeros((w.params.ny, w.params.nx), np.uint8)
+    a = clbm.from_workload(w, precision, rounding=rounding)
+    b = clbm.from_workload(m, precision, rounding=rounding)
+    a.step(41)
+    b.step(41)
+    for x, y in zip(a.moments(), b.moments()):
+        np.testing.assert_array_equal(x, y)
