@@ -182,6 +182,17 @@ clbm_status clbm_nusselt(clbm_ctx* ctx, int32_t which, double length, double dT,
  * r_out = +inf) if any field value is NaN or Inf.  Synchronises. */
 clbm_status clbm_residual(clbm_ctx* ctx, double* r_out);
 
+/* Conservation sums (Eq. 7's conserved moments, Eq. 23's zeroth thermal
+ * moment): FP64 sums over the fluid nodes of the stored post-collision
+ * distributions, out[0] = sum f_i (mass), out[1] = sum f_i e_ix,
+ * out[2] = sum f_i e_iy (momentum; = sum (rho u + F/2)), out[3] = sum g_j
+ * (= sum (T + Q/2), plus half the viscous source where it is on).  On a
+ * lattice without walls the mass is constant, the momentum grows by the summed
+ * body force and out[3] by N Q per step.  `out` is a host array of 4 doubles.
+ * Fixed-order reduction (same value on every call for the same state).
+ * Returns CLBM_EUNSTABLE if a value is NaN or Inf.  Synchronises. */
+clbm_status clbm_totals(clbm_ctx* ctx, double* out);
+
 /* Allocation-free variant of the residual reduction (the paper has no
  * counterpart; it is a service for callers of this library).
  *

@@ -49,7 +49,7 @@ class clbm_batch_item(C.Structure):
 
 
 EXPORTS = ["clbm_create", "clbm_set_boundaries", "clbm_init_fields", "clbm_step", "clbm_moments",
-           "clbm_nusselt", "clbm_residual", "clbm_residual_fields_noalloc", "clbm_batch_create",
+           "clbm_nusselt", "clbm_residual", "clbm_totals", "clbm_residual_fields_noalloc", "clbm_batch_create",
            "clbm_batch_solve", "clbm_batch_lattice", "clbm_batch_tile_width", "clbm_batch_destroy",
            "clbm_damp_period2", "clbm_batch_damp_period2",
            "clbm_batch_last_error", "clbm_time", "clbm_destroy", "clbm_last_error",
@@ -85,6 +85,7 @@ def load(path: Optional[str] = None):
     L.clbm_moments.argtypes = [vp, vp, vp, vp, vp, C.c_int32]
     L.clbm_nusselt.argtypes = [vp, C.c_int32, C.c_double, C.c_double, dp]
     L.clbm_residual.argtypes = [vp, dp]
+    L.clbm_totals.argtypes = [vp, dp]
     L.clbm_residual_fields_noalloc.argtypes = [vp] * 7 + [C.c_int64, vp, dp]
     L.clbm_time.argtypes = [vp, C.POINTER(C.c_int64)]
     L.clbm_destroy.argtypes = [vp]
@@ -202,6 +203,13 @@ def clbm_residual(ctx) -> float:
     return out.value
 
 
+def clbm_totals(ctx) -> np.ndarray:
+    """(sum f_i, sum f_i e_ix, sum f_i e_iy, sum g_j) over the fluid nodes, FP64."""
+    out = np.zeros(4, np.float64)
+    _check(load().clbm_totals(ctx, out.ctypes.data_as(C.POINTER(C.c_double))), ctx, "clbm_totals")
+    return out
+
+
 def clbm_residual_fields_noalloc(T_now, ux_now, uy_now, T_prev, ux_prev, uy_prev, solid, n: int,
                                  stream: Optional[int] = None) -> float:
     """Residual from caller-owned device fields, without device allocation."""
@@ -284,6 +292,9 @@ class Solver:
 
     def residual(self) -> float:
         return clbm_residual(self.ctx)
+
+    def totals(self) -> np.ndarray:
+        return clbm_totals(self.ctx)
 
     @property
     def time(self) -> int:

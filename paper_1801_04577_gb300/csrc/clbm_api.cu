@@ -761,6 +761,27 @@ clbm_status clbm_residual(clbm_ctx* c, double* r_out) {
   return CLBM_OK;
 }
 
+clbm_status clbm_totals(clbm_ctx* c, double* out) {
+  if (!c || !out) return fail(c, CLBM_EINVAL, "bad totals arguments");
+  const long long n = (long long)c->p.nx * c->p.ny;
+  const int nb = red_blocks(n);
+  double* red = c->d_part + kMaxRedBlocks * 8;
+  CLBM_CUDA(c, c->L->totals(make_geom(c), c->buf[c->cur], c->d_part, nb, c->stream));
+  CLBM_CUDA(c, launch_reduce_partials(c->d_part, nb, 8, red, c->stream));
+  double h[8];
+  CLBM_CUDA(c, cudaMemcpyAsync(h, red, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+  CLBM_CUDA(c, cudaStreamSynchronize(c->stream));
+  // the stored values are deviations from the rest state: f_i = w_i rho0 + d_i,
+  // g_j = w_j T0 + h_j (the rest state carries no momentum)
+  out[0] = h[4] * c->p.rho0 + h[0];
+  out[1] = h[1];
+  out[2] = h[2];
+  out[3] = h[4] * c->p.T0 + h[3];
+  if (h[5] != 0.0 || !std::isfinite(out[0] + out[1] + out[2] + out[3]))
+    return fail(c, CLBM_EUNSTABLE, "non-finite field values");
+  return CLBM_OK;
+}
+
 }  // extern "C"
 
 namespace clbm {

@@ -138,6 +138,10 @@ struct Launchers {
                           double* partials, int nblocks, cudaStream_t s);
   cudaError_t (*nusselt)(const DevGeom& g, const DevCoef& c, const void* buf, const NuLink* links,
                          int nlinks, double* partials, int nblocks, cudaStream_t s);
+  // conservation partial sums: out[b*8 + k], k = sum of d_i, d_i e_ix, d_i e_iy, h_j over the fluid
+  // nodes, fluid-node count, non-finite count
+  cudaError_t (*totals)(const DevGeom& g, const void* buf, double* partials, int nblocks,
+                        cudaStream_t s);
   size_t elem_bytes;
   // batched interior step over a tile list (tile = {lattice, row, first x, 0}; tiles skip the
   // first and last column); V = nodes per lane

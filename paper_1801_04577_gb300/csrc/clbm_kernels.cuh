@@ -1055,6 +1055,37 @@ __global__ void __launch_bounds__(kRedThreads)
   block_sum_store<8>(acc, partials + 8 * blockIdx.x);
 }
 
+// Conservation sums over the fluid nodes of the stored post-collision
+// deviations, accumulated in FP64: Sum_i d_i, Sum_i d_i e_ix, Sum_i d_i e_iy,
+// Sum_j h_j, the fluid-node count and the count of non-finite values.
+template <typename S>
+__global__ void __launch_bounds__(kRedThreads)
+    totals_kernel(const DevGeom g, const S* __restrict__ b, double* __restrict__ partials) {
+  double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  const long long n = (long long)g.ny * g.nx;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+       k += (long long)gridDim.x * blockDim.x) {
+    const int y = (int)(k / g.nx), x = (int)(k - (long long)y * g.nx);
+    const long long i = (long long)y * g.pitch + x;
+    if (g.flags && (g.flags[i] & kFlagSolid)) continue;
+    double f[9], s = 0.0;
+#pragma unroll
+    for (int q = 0; q < 9; ++q) f[q] = (double)to_r(b[q * g.plane + i]);
+#pragma unroll
+    for (int q = 9; q < 14; ++q) s += (double)to_r(b[q * g.plane + i]);
+    const double m = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
+    const double jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
+    const double jy = (f[2] - f[4]) + (f[5] - f[7]) + (f[6] - f[8]);
+    acc[0] += m;
+    acc[1] += jx;
+    acc[2] += jy;
+    acc[3] += s;
+    acc[4] += 1.0;
+    if (!isfinite(m) || !isfinite(jx) || !isfinite(jy) || !isfinite(s)) acc[5] += 1.0;
+  }
+  block_sum_store<8>(acc, partials + 8 * blockIdx.x);
+}
+
 template <typename S>
 __global__ void __launch_bounds__(kRedThreads)
     nusselt_kernel(const DevGeom g, const DevCoef c, const S* __restrict__ b,
@@ -1332,6 +1363,12 @@ struct LaunchImpl {
     return cudaGetLastError();
   }
 
+  static cudaError_t totals(const DevGeom& g, const void* buf, double* partials, int nblocks,
+                            cudaStream_t s) {
+    totals_kernel<S><<<nblocks, kRedThreads, 0, s>>>(g, static_cast<const S*>(buf), partials);
+    return cudaGetLastError();
+  }
+
   static cudaError_t nusselt(const DevGeom& g, const DevCoef& c, const void* buf,
                              const NuLink* links, int nlinks, double* partials, int nblocks,
                              cudaStream_t s) {
@@ -1422,6 +1459,7 @@ struct LaunchImpl {
     L.moments = &moments;
     L.residual = &residual;
     L.nusselt = &nusselt;
+    L.totals = &totals;
     L.elem_bytes = sizeof(S);
     return L;
   }
