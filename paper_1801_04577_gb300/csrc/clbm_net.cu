@@ -165,21 +165,24 @@ struct GatherIm2col {
       if (rv && sy >= 0 && sy < x.H && sx >= 0 && sx < x.W) vm |= 1u << t;
     }
     if ((C & 7) == 0) {
+      // all 64 loads of the slice are issued before any is packed (the gather
+      // is bound by load latency, not by issue)
       int t = k0 / C, c = k0 - t * C;
+      float v[tc::kBK / 8][8];
 #pragma unroll
       for (int kc = 0; kc < tc::kBK / 8; ++kc) {
         const bool ok = k0 + kc * 8 < kend && ((vm >> t) & 1u);
         const float* s = src + c * hw + (t / KS - R) * x.W + (t % KS - R);
-        float v[8];
 #pragma unroll
-        for (int e = 0; e < 8; ++e) v[e] = ok ? __ldg(s + e * hw) : 0.0f;
-        put_chunk(dst, r, kc, v);
+        for (int e = 0; e < 8; ++e) v[kc][e] = ok ? __ldg(s + e * hw) : 0.0f;
         c += 8;
         if (c == C) {
           c = 0;
           ++t;
         }
       }
+#pragma unroll
+      for (int kc = 0; kc < tc::kBK / 8; ++kc) put_chunk(dst, r, kc, v[kc]);
     } else {  // channels not a multiple of 8: walk (tap, channel) element by element
       int t = k0 / C, c = k0 - t * C;
       int off = (t / KS - R) * x.W + (t % KS - R);
@@ -211,30 +214,55 @@ struct GatherIm2colT {
   __device__ __forceinline__ void operator()(uint8_t* dst, int row0, int rows_valid, int, int k0,
                                              int kend) const {
     constexpr int KK = KS * KS, R = KS / 2;
+    constexpr int kGroup = 4;  // tasks whose loads are in flight together
+    static_assert((tc::kBM * 8) % (kGroup * tc::kThreads) == 0, "whole groups of tasks");
+    static_assert(tc::kThreads % 8 == 0, "a thread keeps its pixel chunk across tasks");
     const int hw = x.H * x.W;
-    for (int task = threadIdx.x; task < tc::kBM * 8; task += tc::kThreads) {
-      const int r = task >> 3, kc = task & 7;
-      const int row = row0 + r;
-      const int c = row / KK, t = row - c * KK;
-      const int dy = t / KS - R, dx = t % KS - R;
-      const int k = k0 + kc * 8;
-      int nb = k / hw, p = k - nb * hw;
-      int yy = p / x.W, xx = p - yy * x.W;
-      float v[8];
+    // every task of this thread covers the same 8 pixels k .. k + 7 (task & 7 is
+    // threadIdx.x & 7); with W a multiple of 8 they lie in one image row
+    const int k = k0 + (threadIdx.x & 7) * 8;
+    const int nb = k / hw, p = k - nb * hw;
+    const int yy = p / x.W, xx = p - yy * x.W;
+    const bool row8 = (x.W & 7) == 0 && k + 8 <= kend;
+    for (int task0 = threadIdx.x; task0 < tc::kBM * 8; task0 += kGroup * tc::kThreads) {
+      float v[kGroup][8];
 #pragma unroll
-      for (int e = 0; e < 8; ++e) {
-        const int sy = yy + dy, sx = xx + dx;
-        const bool ok = r < rows_valid && k + e < kend && sy >= 0 && sy < x.H && sx >= 0 && sx < x.W;
-        v[e] = ok ? __ldg(x.base + ((long long)nb * x.cs + x.coff + c) * hw + sy * x.W + sx) : 0.0f;
-        if (++xx == x.W) {
-          xx = 0;
-          if (++yy == x.H) {
-            yy = 0;
-            ++nb;
+      for (int u = 0; u < kGroup; ++u) {
+        const int task = task0 + u * tc::kThreads;
+        const int r = task >> 3;
+        const int row = row0 + r;
+        const int c = row / KK, t = row - c * KK;
+        const int dy = t / KS - R, dx = t % KS - R;
+        if (row8) {
+          // one row segment: the row test once, the columns as the range [lo, hi) of e
+          const int sy = yy + dy, sx0 = xx + dx;
+          const bool ok = r < rows_valid && sy >= 0 && sy < x.H;
+          const int lo = sx0 < 0 ? -sx0 : 0, hi = min(8, x.W - sx0);
+          const float* src = x.base + ((long long)nb * x.cs + x.coff + c) * hw + (long long)sy * x.W + sx0;
+#pragma unroll
+          for (int e = 0; e < 8; ++e) v[u][e] = (ok && e >= lo && e < hi) ? __ldg(src + e) : 0.0f;
+        } else {  // pixels may cross rows or samples: element by element
+          int nb1 = nb, yy1 = yy, xx1 = xx;
+#pragma unroll
+          for (int e = 0; e < 8; ++e) {
+            const int sy = yy1 + dy, sx = xx1 + dx;
+            const bool ok = r < rows_valid && k + e < kend && sy >= 0 && sy < x.H && sx >= 0 && sx < x.W;
+            v[u][e] = ok ? __ldg(x.base + ((long long)nb1 * x.cs + x.coff + c) * hw + sy * x.W + sx) : 0.0f;
+            if (++xx1 == x.W) {
+              xx1 = 0;
+              if (++yy1 == x.H) {
+                yy1 = 0;
+                ++nb1;
+              }
+            }
           }
         }
       }
-      put_chunk(dst, r, kc, v);
+#pragma unroll
+      for (int u = 0; u < kGroup; ++u) {
+        const int task = task0 + u * tc::kThreads;
+        put_chunk(dst, task >> 3, task & 7, v[u]);
+      }
     }
   }
 };
@@ -249,26 +277,38 @@ struct GatherRows {
                                              int kend) const {
     const int hw = a.H * a.W;
     const bool vec = (hw & 7) == 0;
-    for (int task = threadIdx.x; task < nrows * 8; task += tc::kThreads) {
-      const int r = task >> 3, kc = task & 7;
-      const int k = k0 + kc * 8;
-      const long long ch = a.coff + row0 + r;
-      float v[8];
-      if (r < rows_valid && vec && k + 8 <= kend) {
-        const int nb = k / hw, p = k - nb * hw;
-        const float4* s4 = reinterpret_cast<const float4*>(a.base + ((long long)nb * a.cs + ch) * hw + p);
-        const float4 u0 = __ldg(s4), u1 = __ldg(s4 + 1);
-        v[0] = u0.x; v[1] = u0.y; v[2] = u0.z; v[3] = u0.w;
-        v[4] = u1.x; v[5] = u1.y; v[6] = u1.z; v[7] = u1.w;
-      } else {
+    constexpr int kGroup = 4;  // tasks whose loads are in flight together
+    const int ntask = nrows * 8;
+    for (int task0 = threadIdx.x; task0 < ntask; task0 += kGroup * tc::kThreads) {
+      float v[kGroup][8];
 #pragma unroll
-        for (int e = 0; e < 8; ++e) {
-          const int kk = k + e;
-          const int nb = kk / hw, p = kk - nb * hw;
-          v[e] = (r < rows_valid && kk < kend) ? __ldg(a.base + ((long long)nb * a.cs + ch) * hw + p) : 0.0f;
+      for (int u = 0; u < kGroup; ++u) {
+        const int task = task0 + u * tc::kThreads;
+        const int r = task >> 3, kc = task & 7;
+        const int k = k0 + kc * 8;
+        const long long ch = a.coff + row0 + r;
+        if (task < ntask && r < rows_valid && vec && k + 8 <= kend) {
+          const int nb = k / hw, p = k - nb * hw;
+          const float4* s4 = reinterpret_cast<const float4*>(a.base + ((long long)nb * a.cs + ch) * hw + p);
+          const float4 u0 = __ldg(s4), u1 = __ldg(s4 + 1);
+          v[u][0] = u0.x; v[u][1] = u0.y; v[u][2] = u0.z; v[u][3] = u0.w;
+          v[u][4] = u1.x; v[u][5] = u1.y; v[u][6] = u1.z; v[u][7] = u1.w;
+        } else {
+#pragma unroll
+          for (int e = 0; e < 8; ++e) {
+            const int kk = k + e;
+            const int nb = kk / hw, p = kk - nb * hw;
+            v[u][e] = (task < ntask && r < rows_valid && kk < kend)
+                          ? __ldg(a.base + ((long long)nb * a.cs + ch) * hw + p)
+                          : 0.0f;
+          }
         }
       }
-      put_chunk(dst, r, kc, v);
+#pragma unroll
+      for (int u = 0; u < kGroup; ++u) {
+        const int task = task0 + u * tc::kThreads;
+        if (task < ntask) put_chunk(dst, task >> 3, task & 7, v[u]);
+      }
     }
   }
 };
