@@ -775,13 +775,15 @@ tc::Packed packed_of(const clbm_net* net, int layer, int transpose) {
 }
 
 // K range per split of a weight-gradient GEMM (K = pixels): the FP32 kernel
-// takes 4096 pixels per split; the tensor-core one enough splits to give
-// about eight CTAs per SM (its gathers are latency-bound), at least four
-// 64-wide K slices each.
+// takes 4096 pixels per split; the tensor-core one enough splits for about one
+// wave of CTAs (five resident per SM, the shared-memory limit), at least four
+// 64-wide K slices each (measured: 3, 5, 8 and 10 CTAs per SM gave 2.53,
+// 2.55, 2.60 and 2.57 ms per 64^2 training step, 6.86, 6.80, 7.01 and
+// 6.83 ms at 128^2).
 long long dw_kper(bool tensor, long long Np, int Kd, int co) {
   if (!tensor) return 4096;
   const long long tiles = (long long)((Kd + tc::kBM - 1) / tc::kBM) * ((co + tc::kMaxBN - 1) / tc::kMaxBN);
-  long long splits = std::max<long long>(1, (8 * 152 + tiles - 1) / tiles);
+  long long splits = std::max<long long>(1, (5 * 152 + tiles - 1) / tiles);
   splits = std::min<long long>(splits, std::max<long long>(1, Np / 256));
   const long long per = (Np + splits - 1) / splits;
   return ((per + tc::kBK - 1) / tc::kBK) * tc::kBK;
