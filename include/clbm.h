@@ -25,7 +25,7 @@
  *   - Streams: all device work of a context is issued on its stream (the one
  *     passed to clbm_create, or a stream the library creates for NULL).
  *     clbm_step only enqueues work; calls that return a host value
- *     (clbm_moments to host, clbm_nusselt, clbm_residual) synchronise the
+ *     (clbm_moments to host, clbm_nusselt, clbm_residual, clbm_totals) synchronise the
  *     stream before returning.
  *   - Errors: no call throws or aborts.  Each returns a clbm_status; on a
  *     failure the context (when there is one) keeps a message readable with
