@@ -574,13 +574,57 @@ __global__ void up_back_kernel(Act gout, float* __restrict__ gin, int gcs, int g
 
 // masked MSE: loss = sum mask (y - t)^2 / (sum mask * C); g = dloss/dy.  One block
 // per sample writes FP64 partials (fixed order), summed on the host.
-__global__ void loss_kernel(const float* __restrict__ y, const float* __restrict__ t,
-                            const float* __restrict__ mask, int C, int HW, double inv_norm,
-                            float* __restrict__ g, double* __restrict__ part) {
+// Loss chunks per sample (blockIdx.y of the mask and loss kernels).
+constexpr int kLossChunks = 16;
+
+// Block sum of a double in fixed order (GT threads).
+__device__ double block_sum_fixed(double s) {
   __shared__ double sh[GT];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = GT / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  const double r = sh[0];
+  __syncthreads();
+  return r;
+}
+
+// Mask weight sum of each sample: part[nb] = sum of mask over sample nb's pixels.
+__global__ void mask_sum_kernel(const float* __restrict__ mask, int HW, double* __restrict__ part) {
   const int nb = blockIdx.x;
   double s = 0.0;
-  for (int k = threadIdx.x; k < C * HW; k += blockDim.x) {
+  for (int p = threadIdx.x; p < HW; p += blockDim.x) s += mask[(long long)nb * HW + p];
+  s = block_sum_fixed(s);
+  if (threadIdx.x == 0) part[nb] = s;
+}
+
+// Masked MSE over N samples of C channels: every block first forms the
+// normaliser norm = C * sum of the N mask sums (or C * N * HW without a mask)
+// in the same fixed order, then its chunk of sample nb gives
+// g = 2 mask (y - t) / norm and the chunk's sum of mask (y - t)^2 in
+// part[nb * kLossChunks + chunk]; the host divides the sum of the parts by the
+// same normaliser.
+__global__ void loss_kernel(const float* __restrict__ y, const float* __restrict__ t,
+                            const float* __restrict__ mask, const double* __restrict__ mpart, int N,
+                            int C, int HW, float* __restrict__ g, double* __restrict__ part) {
+  __shared__ double inv_norm;
+  if (threadIdx.x == 0) {
+    double m = 0.0;
+    if (mask) {
+      for (int i = 0; i < N; ++i) m += mpart[i];
+    } else {
+      m = (double)N * HW;
+    }
+    inv_norm = 1.0 / (m * C);
+  }
+  __syncthreads();
+  const int nb = blockIdx.x, ch = blockIdx.y;
+  const int tot = C * HW;
+  const int per = (tot + kLossChunks - 1) / kLossChunks, k0 = ch * per, k1 = min(tot, k0 + per);
+  double s = 0.0;
+  for (int k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
     const int c = k / HW, p = k - c * HW;
     const long long i = ((long long)nb * C + c) * HW + p;
     const double w = mask ? mask[(long long)nb * HW + p] : 1.0;
@@ -588,13 +632,8 @@ __global__ void loss_kernel(const float* __restrict__ y, const float* __restrict
     s += w * d * d;
     g[i] = (float)(2.0 * w * d * inv_norm);
   }
-  sh[threadIdx.x] = s;
-  __syncthreads();
-  for (int o = GT / 2; o > 0; o >>= 1) {
-    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) part[nb] = sh[0];
+  s = block_sum_fixed(s);
+  if (threadIdx.x == 0) part[nb * kLossChunks + ch] = s;
 }
 
 // Adam on the FP32 master parameters, refreshing the BF16 copy.
@@ -669,7 +708,7 @@ struct clbm_net {
   std::vector<int> act_c, act_hw;              // channels and H (= W) of each buffer
   float* part = nullptr;                       // split-K partials
   long long part_cap = 0;
-  double* loss_part = nullptr;
+  double* loss_part = nullptr;  // [max_batch][kLossChunks] loss partials, then [max_batch] mask sums
   int* tflag = nullptr;  // mapped pinned host flag: a tensor-core wait timed out
   int* d_tflag = nullptr;
   int64_t steps = 0;
@@ -1126,7 +1165,8 @@ clbm_status clbm_net_create(const clbm_net_config* cfg, uint64_t seed, void* str
   if (cudaHostAlloc(&n->tflag, sizeof(int), cudaHostAllocMapped) != cudaSuccess) return bail(CLBM_ENOMEM);
   *n->tflag = 0;
   if (cudaHostGetDevicePointer(&n->d_tflag, n->tflag, 0) != cudaSuccess) return bail(CLBM_ECUDA);
-  if (cudaMalloc(&n->part, cap * sizeof(float)) || cudaMalloc(&n->loss_part, c.max_batch * sizeof(double)))
+  if (cudaMalloc(&n->part, cap * sizeof(float)) ||
+      cudaMalloc(&n->loss_part, (size_t)c.max_batch * (kLossChunks + 1) * sizeof(double)))
     return bail(CLBM_ENOMEM);
   if (cudaStreamSynchronize(n->stream) != cudaSuccess) return bail(CLBM_ECUDA);
   *out = n;
@@ -1180,31 +1220,40 @@ clbm_status clbm_net_gradients(clbm_net* n, const float* x, const float* target,
   const long long in_e = (long long)N * n->cfg.in_ch * G * G;
   cudaError_t e = cudaMemcpyAsync(n->act[P.in], x, in_e * sizeof(float), cudaMemcpyDeviceToDevice, n->stream);
   if (!e) e = forward(n, P, N);
-  // loss normalisation: sum of mask weights times channels
+  // loss normalisation (sum of mask weights times channels) on the device, so
+  // that the backward pass follows the forward pass without a host round trip
+  double* mpart = n->loss_part + (size_t)n->cfg.max_batch * kLossChunks;
+  if (!e && mask) {
+    mask_sum_kernel<<<N, GT, 0, n->stream>>>(mask, G * G, mpart);
+    e = cudaGetLastError();
+  }
+  if (!e) {
+    loss_kernel<<<dim3(N, kLossChunks), GT, 0, n->stream>>>(n->act[P.out], target, mask, mpart, N, C, G * G,
+                                                            n->gact[P.out], n->loss_part);
+    e = cudaGetLastError();
+  }
+  if (!e) e = backward(n, P, N);
+  std::vector<double> lp((size_t)N * kLossChunks + N);
+  if (!e)
+    e = cudaMemcpyAsync(lp.data(), n->loss_part, (size_t)N * kLossChunks * sizeof(double), cudaMemcpyDeviceToHost,
+                        n->stream);
+  if (!e && mask)
+    e = cudaMemcpyAsync(lp.data() + (size_t)N * kLossChunks, mpart, (size_t)N * sizeof(double),
+                        cudaMemcpyDeviceToHost, n->stream);
+  if (!e) e = cudaStreamSynchronize(n->stream);
+  if (e) return cuda_status(n, e, "gradients");
+  if (timed_out(n)) return nfail(n, CLBM_ETIMEOUT, kTimeoutMsg);
+  // the normaliser in the loss kernel's order
   double norm = 0.0;
   if (mask) {
-    std::vector<float> hm((size_t)N * G * G);
-    if (!e) e = cudaMemcpyAsync(hm.data(), mask, hm.size() * sizeof(float), cudaMemcpyDeviceToHost, n->stream);
-    if (!e) e = cudaStreamSynchronize(n->stream);
-    for (float w : hm) norm += w;
+    for (int i = 0; i < N; ++i) norm += lp[(size_t)N * kLossChunks + i];
   } else {
     norm = (double)N * G * G;
   }
   norm *= C;
   if (!(norm > 0)) return nfail(n, CLBM_EINVAL, "empty loss mask");
-  if (!e) {
-    loss_kernel<<<N, GT, 0, n->stream>>>(n->act[P.out], target, mask, C, G * G, 1.0 / norm,
-                                         n->gact[P.out], n->loss_part);
-    e = cudaGetLastError();
-  }
-  if (!e) e = backward(n, P, N);
-  std::vector<double> lp(N);
-  if (!e) e = cudaMemcpyAsync(lp.data(), n->loss_part, N * sizeof(double), cudaMemcpyDeviceToHost, n->stream);
-  if (!e) e = cudaStreamSynchronize(n->stream);
-  if (e) return cuda_status(n, e, "gradients");
-  if (timed_out(n)) return nfail(n, CLBM_ETIMEOUT, kTimeoutMsg);
   double s = 0.0;
-  for (double v : lp) s += v;
+  for (int i = 0; i < N * kLossChunks; ++i) s += lp[i];
   if (loss) *loss = s / norm;
   if (grad) {
     e = cudaMemcpy(grad, n->g, n->nparam * sizeof(float), cudaMemcpyDefault);
