@@ -334,9 +334,10 @@ clbm_status clbm_net_set_params(clbm_net* net, const float* src, int32_t on_devi
 clbm_status clbm_net_forward(clbm_net* net, const float* x, int32_t n, float* y);
 
 /* Loss and parameter gradients: loss = sum mask (y - t)^2 / (sum mask * out_ch)
- * with mask[N][G][G] (NULL = all ones).  grad (param_count floats, host or
- * device, may be NULL) receives dloss/dparams; *loss (may be NULL) the loss.
- * Synchronises. */
+ * with mask[N][G][G] (NULL = all ones; the sums are formed on the device, and
+ * a mask that sums to zero returns CLBM_EINVAL with the gradients undefined).
+ * grad (param_count floats, host or device, may be NULL) receives
+ * dloss/dparams; *loss (may be NULL) the loss.  Synchronises once, at the end. */
 clbm_status clbm_net_gradients(clbm_net* net, const float* x, const float* target,
                                const float* mask, int32_t n, float* grad, double* loss);
 
