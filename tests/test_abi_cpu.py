@@ -65,3 +65,7 @@ def test_null_arguments():
     assert L.clbm_destroy(None) == clbm.CLBM_OK
     assert L.clbm_step(None, 1) == clbm.CLBM_EINVAL
     assert L.clbm_last_error(None) == b""
+    out = (C.c_double * 4)()
+    assert L.clbm_totals(None, out) == clbm.CLBM_EINVAL
+    assert L.clbm_residual(None, out) == clbm.CLBM_EINVAL
+    assert L.clbm_nusselt(None, 0, 1.0, 1.0, out) == clbm.CLBM_EINVAL
