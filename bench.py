@@ -223,7 +223,7 @@ def run_reference(args):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": el / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"rayleigh_benard_4096x2048_Ra1e6_{args.precision}",
+            "config": {"workload": f"rayleigh_benard_4096x2048_Ra{1e6:g}_{args.precision}",
                        "sample": f"{nx}x{ny} lattice of the same workload"},
             "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": cores, "kind": "oracle",
                              "sample": f"FP64 oracle, Rayleigh-Benard {nx}x{ny}, {args.steps} steps "
@@ -252,26 +252,31 @@ def combine_ranks(elapsed_ms: float, nodes: int, steps: int, device=None):
 
 
 def box_lattice(w) -> bool:
-    """No solid mask and no listed links: the library fuses interior and
-    boundary work into one launch per step."""
+    """No solid mask and no listed links (a plain box lattice)."""
     return w.geom.solid is None and len(w.geom.link_node) == 0
 
 
 def step_kernel_name(w) -> str:
+    """Box and masked lattices alike take one fused launch per step: the
+    listed boundary nodes in the first blocks, the interior warp tiles in the
+    rest (masked lattices skip tiles without fluid and leave flagged nodes to
+    the boundary blocks)."""
     if box_lattice(w):
         return "step_fused_kernel (interior tiles + boundary nodes, one launch per step)"
-    return "step_kernel + boundary_kernel (two launches per step)"
+    return "step_fused_kernel<masked> (tile classes + listed boundary nodes, one launch per step)"
 
 
-def step_launches(w, steps: int, graph_steps: int = 32) -> int:
-    """Kernels that clbm_step(steps) launches: per step one fused launch (box
-    lattices) or the interior and boundary kernels; runs of graph_steps or more
-    replay a captured graph that adds one step-counter kernel per graph, after
-    one kernel that sets the counter."""
-    per_step = 1 if box_lattice(w) else 2
-    n = per_step * steps
-    if steps >= graph_steps:
-        n += 1 + steps // graph_steps
+def step_launches(w, steps: int, graph_levels: int = 5) -> int:
+    """Kernels that clbm_step(steps) launches: one fused launch per step.  A
+    run of two or more steps replays captured graphs of 32, 16, ..., 2 steps
+    (the binary digits of `steps`; a last odd step is launched on its own),
+    each ending with one step-counter kernel, after one kernel that sets the
+    counter."""
+    n = steps
+    if steps >= 2:
+        top = 1 << graph_levels
+        graphs = steps // top + bin((steps % top) >> 1).count("1")
+        n += 1 + graphs
     return n
 
 
@@ -304,13 +309,14 @@ def run_native(args):
     stream = torch.cuda.Stream(dev)
     torch.cuda.set_stream(stream)
     s = clbm.from_workload(w, args.precision, stream=stream.cuda_stream, rounding=args.rounding)
+    # clocks are sampled from before the warm-up to the end of the timed region
+    sampler = ClockSampler(device_index(local))
+    sampler.start()
     s.step(args.warmup)
     torch.cuda.synchronize()
     barrier()
     torch.cuda.synchronize()
 
-    sampler = ClockSampler(device_index(local))
-    sampler.start()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)

@@ -205,13 +205,17 @@ clbm_status clbm_totals(clbm_ctx* ctx, double* out);
  * FP64 device arrays of n values (for instance two clbm_moments snapshots one
  * step apart); `solid` is an optional device uint8 mask (nonzero = skip).
  * The result is written to the host double *r_out; the call synchronises
- * `stream` (a cudaStream_t, NULL = legacy default stream).
+ * `stream` (a cudaStream_t, NULL = legacy default stream), which must belong
+ * to the current device (else CLBM_EINVAL).  Because it copies the result to
+ * the host and synchronises, it must not be called while any stream of the
+ * process is being captured into a CUDA graph.
  *
  * It calls no cudaMalloc, cudaFree or allocating library routine: its
  * reduction scratch is a fixed 65,600-byte array in the library's device
  * data, held on every GPU that loads the library until the process exits.
  * The first call on a device looks that array's address up (once per device,
- * with the device current); make that first call before any stream capture.
+ * with the device current) and caches it; after a cudaDeviceReset of that
+ * device the cached address is stale, so do not use this call after a reset.
  * All calls share the array, so calls that overlap on the GPU race and must be
  * serialised by the caller.  Limits: 1 <= n <= 2^31, else CLBM_EINVAL;
  * CLBM_EUNSTABLE (r_out = +inf) if a value is NaN or Inf. */

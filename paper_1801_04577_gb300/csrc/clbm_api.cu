@@ -27,6 +27,9 @@ constexpr int kEX[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
 constexpr int kEY[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
 constexpr int kOpp[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
 constexpr int kMaxRedBlocks = 1024;
+// Step graphs: level l holds 2^(l+1) steps, l = 0 .. kGraphLevels - 1 (2 .. 32 steps).
+constexpr int kGraphLevels = 5;
+constexpr int kGraphSteps = 1 << kGraphLevels;
 
 }  // namespace
 
@@ -64,20 +67,19 @@ struct clbm_ctx {
   double* d_fields = nullptr;  // 4 * nx * ny doubles, allocated on first use
   double* d_part = nullptr;    // reduction partials + result
   std::map<int, std::pair<NuLink*, int>> nu_lists;
-  // captured graphs of kGraphSteps steps, keyed by (current buffer, step parity)
+  // captured step graphs of 2, 4, ..., kGraphSteps steps, keyed by (current buffer, step parity)
   long long* d_t = nullptr;
-  cudaGraphExec_t step_graph[4] = {nullptr, nullptr, nullptr, nullptr};
+  cudaGraphExec_t step_graph[4][kGraphLevels] = {};
   std::string err;
 };
 
-constexpr int kGraphSteps = 32;
-
 static void drop_graphs(clbm_ctx* c) {
-  for (auto& g : c->step_graph)
-    if (g) {
-      cudaGraphExecDestroy(g);
-      g = nullptr;
-    }
+  for (auto& key : c->step_graph)
+    for (auto& g : key)
+      if (g) {
+        cudaGraphExecDestroy(g);
+        g = nullptr;
+      }
 }
 
 static clbm_status fail(clbm_ctx* c, clbm_status s, const std::string& msg) {
@@ -549,19 +551,19 @@ static StepArgs step_args(const clbm_ctx* c, int cur, int64_t t) {
   return a;
 }
 
-// Capture kGraphSteps steps starting from buffer `cur` at a step of parity `par`.
-static clbm_status capture_steps(clbm_ctx* c, int cur, int par, cudaGraphExec_t* out) {
+// Capture `len` steps starting from buffer `cur` at a step of parity `par`.
+static clbm_status capture_steps(clbm_ctx* c, int cur, int par, int len, cudaGraphExec_t* out) {
   if (!c->d_t) CLBM_CUDA(c, cudaMalloc(&c->d_t, sizeof(long long)));
   cudaGraph_t graph;
   CLBM_CUDA(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
   cudaError_t e = cudaSuccess;
-  for (int j = 0; j < kGraphSteps && e == cudaSuccess; ++j) {
+  for (int j = 0; j < len && e == cudaSuccess; ++j) {
     StepArgs a = step_args(c, (cur + j) & 1, par + j);
     a.tdev = c->d_t;
     a.tstep = j;
     e = c->L->step(a, c->stream);
   }
-  if (e == cudaSuccess) e = launch_advance(c->d_t, kGraphSteps, c->stream);
+  if (e == cudaSuccess) e = launch_advance(c->d_t, len, c->stream);
   cudaError_t e2 = cudaStreamEndCapture(c->stream, &graph);
   if (e != cudaSuccess || e2 != cudaSuccess) {
     if (e2 == cudaSuccess) cudaGraphDestroy(graph);
@@ -577,23 +579,34 @@ static clbm_status capture_steps(clbm_ctx* c, int cur, int par, cudaGraphExec_t*
 clbm_status clbm_step(clbm_ctx* c, int64_t nsteps) {
   if (!c || nsteps < 0) return fail(c, CLBM_EINVAL, "bad step count");
   if (!c->have_walls) return fail(c, CLBM_EINVAL, "non-periodic lattice: call clbm_set_boundaries first");
-  // Long runs replay a captured graph of kGraphSteps launches (fewer launch
-  // gaps); the step count then lives on the device.  Not while the caller is
-  // capturing the stream itself.
+  // Runs of two or more steps replay captured graphs of 32, 16, ..., 2 steps
+  // (the binary digits of nsteps; fewer launch gaps), with the step count on
+  // the device.  Every graph length is even, so the buffer/parity key stays the
+  // same across them; the graphs of a key and of the key one single step away
+  // are captured together on first use, so later calls of any length start
+  // without a capture.  Not while the caller is capturing the stream itself.
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   CLBM_CUDA(c, cudaStreamIsCapturing(c->stream, &cs));
-  if (nsteps >= kGraphSteps && cs == cudaStreamCaptureStatusNone) {
+  if (nsteps >= 2 && cs == cudaStreamCaptureStatusNone) {
     const int key = c->cur * 2 + (int)(c->t & 1);
-    if (!c->step_graph[key]) {
-      clbm_status st = capture_steps(c, c->cur, (int)(c->t & 1), &c->step_graph[key]);
-      if (st != CLBM_OK) return st;
-    }
+    for (const int k : {key, key ^ 3})
+      for (int l = 0; l < kGraphLevels; ++l)
+        if (!c->step_graph[k][l]) {
+          clbm_status st = capture_steps(c, k >> 1, k & 1, 2 << l, &c->step_graph[k][l]);
+          if (st != CLBM_OK) return st;
+        }
     CLBM_CUDA(c, launch_set_step(c->d_t, c->t, c->stream));
     while (nsteps >= kGraphSteps) {
-      CLBM_CUDA(c, cudaGraphLaunch(c->step_graph[key], c->stream));
-      c->t += kGraphSteps;  // kGraphSteps is even: the current buffer is unchanged
+      CLBM_CUDA(c, cudaGraphLaunch(c->step_graph[key][kGraphLevels - 1], c->stream));
+      c->t += kGraphSteps;  // even: the current buffer is unchanged
       nsteps -= kGraphSteps;
     }
+    for (int l = kGraphLevels - 2; l >= 0; --l)
+      if (nsteps >= (2 << l)) {
+        CLBM_CUDA(c, cudaGraphLaunch(c->step_graph[key][l], c->stream));
+        c->t += 2 << l;
+        nsteps -= 2 << l;
+      }
   }
   for (int64_t s = 0; s < nsteps; ++s) {
     StepArgs a = step_args(c, c->cur, c->t);

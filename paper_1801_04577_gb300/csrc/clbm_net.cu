@@ -712,6 +712,7 @@ struct clbm_net {
   int* tflag = nullptr;  // mapped pinned host flag: a tensor-core wait timed out
   int* d_tflag = nullptr;
   int64_t steps = 0;
+  int sms = 152;  // multiprocessors of the device (one wave = 5 CTAs per SM)
   Plan plan{};
   std::string err;
 };
@@ -775,12 +776,13 @@ cudaError_t tc_gemm(clbm_net* net, GA ga, GB gb, ST st, int M, int N, int K, int
 // least four slices per range) until there is about one wave (measured against
 // two CTAs per SM: 2.43 -> 2.44 ms per 64^2 training step, 6.33 -> 6.23 ms at
 // 128^2).
-int conv_splits(int M, int N, int K) {
+int conv_splits(int sms, int M, int N, int K) {
   const int bn = tc::tile_n(N);
   const long long ctas = (long long)((M + tc::kBM - 1) / tc::kBM) * ((N + bn - 1) / bn);
   const int slices = (K + tc::kBK - 1) / tc::kBK;
-  if (ctas >= 5 * 152 || slices < 8) return 1;
-  const long long s = std::min<long long>((5 * 152 + ctas - 1) / ctas, slices / 4);
+  const long long wave = 5LL * sms;
+  if (ctas >= wave || slices < 8) return 1;
+  const long long s = std::min<long long>((wave + ctas - 1) / ctas, slices / 4);
   if (s <= 1) return 1;
   const int kper = (int)(((K + s - 1) / s + tc::kBK - 1) / tc::kBK) * tc::kBK;
   return (K + kper - 1) / kper;
@@ -790,7 +792,7 @@ int conv_splits(int M, int N, int K) {
 // splitk_finish_kernel.
 template <int KS, class GB>
 cudaError_t tc_conv_gemm(clbm_net* net, Act x, GB gb, StoreAct st, int M, int N, int K) {
-  const int splits = conv_splits(M, N, K);
+  const int splits = conv_splits(net->sms, M, N, K);
   if (splits == 1) return tc_gemm(net, GatherIm2col<KS>{x}, gb, TStoreAct{st}, M, N, K, K);
   if ((long long)splits * M * N > net->part_cap) return cudaErrorInvalidValue;
   const int kper = (K + splits - 1) / splits;
@@ -821,10 +823,10 @@ tc::Packed packed_of(const clbm_net* net, int layer, int transpose) {
 // 64-wide K slices each (measured: 3, 5, 8 and 10 CTAs per SM gave 2.53,
 // 2.55, 2.60 and 2.57 ms per 64^2 training step, 6.86, 6.80, 7.01 and
 // 6.83 ms at 128^2).
-long long dw_kper(bool tensor, long long Np, int Kd, int co) {
+long long dw_kper(int sms, bool tensor, long long Np, int Kd, int co) {
   if (!tensor) return 4096;
   const long long tiles = (long long)((Kd + tc::kBM - 1) / tc::kBM) * ((co + tc::kMaxBN - 1) / tc::kMaxBN);
-  long long splits = std::max<long long>(1, (5 * 152 + tiles - 1) / tiles);
+  long long splits = std::max<long long>(1, (5LL * sms + tiles - 1) / tiles);
   splits = std::min<long long>(splits, std::max<long long>(1, Np / 256));
   const long long per = (Np + splits - 1) / splits;
   return ((per + tc::kBK - 1) / tc::kBK) * tc::kBK;
@@ -854,7 +856,7 @@ cudaError_t conv_backward(clbm_net* net, const Conv& cv, Act x, Act gy, int gx_i
   // weight gradient: M = co, N = ci*t, K = pixels, split-K
   {
     const bool tensor = tensor_math(net);
-    const int kper = (int)dw_kper(tensor, Np, Kd, cv.co);
+    const int kper = (int)dw_kper(net->sms, tensor, Np, Kd, cv.co);
     const int splits = (Np + kper - 1) / kper;
     const long long need = (long long)splits * cv.co * Kd;
     if (need > net->part_cap) return cudaErrorInvalidValue;
@@ -1148,18 +1150,24 @@ clbm_status clbm_net_create(const clbm_net_config* cfg, uint64_t seed, void* str
     n->act.push_back(a);
     n->gact.push_back(ga);
   }
+  {  // one wave of CTAs is sized from the device's multiprocessor count
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && sms > 0)
+      n->sms = sms;
+  }
   // split-K partials: enough for the largest batch (fewer pixels never need more splits)
   long long cap = 0;
   for (const Conv& cv : n->convs) {
     const int Kd = cv.ci * cv.ks * cv.ks;
     for (long long nb = 1; nb <= c.max_batch; ++nb) {
       const long long Np = nb * cv.H * cv.W;
-      const long long kper = dw_kper(c.math == CLBM_NET_TENSOR, Np, Kd, cv.co);
+      const long long kper = dw_kper(n->sms, c.math == CLBM_NET_TENSOR, Np, Kd, cv.co);
       cap = std::max(cap, ((Np + kper - 1) / kper) * cv.co * Kd);
       cap = std::max(cap, ((Np + kBiasChunk - 1) / kBiasChunk) * cv.co);  // bias chunk sums
       if (c.math == CLBM_NET_TENSOR) {  // split-K forward and input-gradient GEMMs
-        cap = std::max(cap, (long long)conv_splits((int)Np, cv.co, Kd) * Np * cv.co);
-        cap = std::max(cap, (long long)conv_splits((int)Np, cv.ci, cv.co * cv.ks * cv.ks) * Np * cv.ci);
+        cap = std::max(cap, (long long)conv_splits(n->sms, (int)Np, cv.co, Kd) * Np * cv.co);
+        cap = std::max(cap, (long long)conv_splits(n->sms, (int)Np, cv.ci, cv.co * cv.ks * cv.ks) * Np * cv.ci);
       }
     }
   }

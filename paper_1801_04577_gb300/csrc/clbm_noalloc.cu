@@ -97,9 +97,14 @@ extern "C" clbm_status clbm_residual_fields_noalloc(const double* T_now, const d
   if (!T_now || !ux_now || !uy_now || !T_prev || !ux_prev || !uy_prev || !r_out)
     return CLBM_EINVAL;
   if (n < 1 || n > kNoAllocMaxNodes) return CLBM_EINVAL;  // beyond the supported lattice size
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // the scratch address is the current device's: the stream must belong to it
+  int cur_dev = 0, stream_dev = 0;
+  if (cudaGetDevice(&cur_dev) != cudaSuccess) return CLBM_ECUDA;
+  if (cudaStreamGetDevice(s, &stream_dev) != cudaSuccess) return CLBM_EINVAL;
+  if (stream_dev != cur_dev) return CLBM_EINVAL;
   double* scratch = nullptr;
   if (scratch_address(&scratch) != cudaSuccess) return CLBM_ECUDA;
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
   long long b = (n + kRedThreads - 1) / kRedThreads;
   const int nblocks = (int)(b < kNoAllocMaxBlocks ? b : kNoAllocMaxBlocks);
   double* result = scratch + kNoAllocMaxBlocks * kNoAllocWidth;

@@ -21,15 +21,16 @@ def rel_inf(a, b, mask=None):
     return float(np.abs(a - b).max() / den)
 
 
-def compare(w, gpu_fields, ora_fields):
-    """Per-field max-norm errors relative to max(||oracle field||_inf, field scale).
+def compare(w, gpu_fields, ora_fields, floor=False):
+    """Per-field max-norm errors ||a - b||_inf / ||b||_inf over the fluid nodes
+    (the density as rho - rho0), each field against its own largest value.
 
-    The scale is the problem's own magnitude for that field: rho0 for the
-    density, the characteristic velocity U for u_x and u_y, and the temperature
-    difference for T.  The state the scheme rounds is O(rho0) and O(T), so a
-    velocity field that is still tiny (early in a run started from rest)
-    cannot be matched better than rounding relative to those scales; for
-    developed flows the oracle's own maximum dominates.
+    floor=True divides by max(||b||_inf, field scale) instead, the scale being
+    rho0 for the density, the characteristic velocity U for u_x and u_y and the
+    temperature difference for T.  A test passes it only where it states why:
+    a velocity field that is still tiny (a few steps from rest) is the
+    difference of O(rho0) populations, so its rounding error is set by rho0
+    and U, not by its own size.
     """
     mask = None if w.geom.solid is None else (w.geom.solid == 0)
     scales = {"rho": w.params.rho0, "ux": w.u_scale, "uy": w.u_scale, "T": w.dT}
@@ -39,12 +40,15 @@ def compare(w, gpu_fields, ora_fields):
             a, b = a - w.params.rho0, b - w.params.rho0
         if mask is not None:
             a, b = a[mask], b[mask]
-        den = max(float(np.abs(b).max()), abs(scales[name]))
-        out[name] = float(np.abs(a - b).max() / den)
+        den = float(np.abs(b).max())
+        if floor:
+            den = max(den, abs(scales[name]))
+        err = float(np.abs(a - b).max())
+        out[name] = err / den if den > 0 else err
     return out
 
 
-def run_pair(w, steps, precision="f64"):
+def run_pair(w, steps, precision="f64", floor=False):
     s = clbm.from_workload(w, precision)
     o = oracle.from_workload(w)
     s.step(steps)
@@ -52,4 +56,4 @@ def run_pair(w, steps, precision="f64"):
     g = s.moments()
     r = o.moments()
     s_obj = (s, o)
-    return compare(w, g, r), s_obj
+    return compare(w, g, r, floor), s_obj

@@ -51,15 +51,27 @@ def test_single_process_has_no_collective():
 
 
 def test_launch_count_claim_follows_the_launch_scheme():
-    """gpu_launches: one fused launch per step on box lattices, two on masked
-    ones, plus the graph's step-counter kernels for runs of 32 steps or more."""
+    """gpu_launches: one fused launch per step on box and masked lattices
+    alike; a run of two or more steps adds one counter-setting kernel and one
+    step-counter kernel per replayed graph (graphs of 32, 16, ..., 2 steps)."""
     import bench
     rb = bench.workload("rb256")
     an = bench.workload("annulus2048")
     assert bench.box_lattice(rb) and not bench.box_lattice(an)
-    assert bench.step_launches(rb, 10) == 10
-    assert bench.step_launches(rb, 64) == 64 + 1 + 2
-    assert bench.step_launches(an, 100) == 200 + 1 + 3
+    assert "step_fused_kernel" in bench.step_kernel_name(an)
+    assert bench.step_launches(rb, 1) == 1
+    assert bench.step_launches(rb, 3) == 3 + 1 + 1          # graph of 2 + one single step
+    assert bench.step_launches(rb, 20) == 20 + 1 + 2        # graphs of 16 and 4
+    assert bench.step_launches(rb, 64) == 64 + 1 + 2        # two graphs of 32
+    assert bench.step_launches(an, 100) == 100 + 1 + 4     # 3 x 32 + 4
+
+
+def test_reference_arm_names_the_same_workload():
+    """Both bench arms spell the benchmark workload the same way."""
+    import bench
+    from paper_1801_04577_gb300 import inputs as I
+    name = I.rayleigh_benard(64, 32).name.replace("64x32", "4096x2048")
+    assert name == f"rayleigh_benard_4096x2048_Ra{1e6:g}"
 
 
 def test_unet_flop_count_by_hand():

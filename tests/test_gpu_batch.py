@@ -70,6 +70,50 @@ def test_batch_against_oracle_f64():
     b.close()
 
 
+def test_batch_against_oracle_f32():
+    """FP32 lattices of a batch (random initial fields with walls, obstacle and
+    source; a cavity from rest; a noisy Rayleigh-Benard cell with a periodic
+    seam) against the FP64 oracle, every field against its own largest value."""
+    ws = [I.obstacle_channel(), I.natural_convection_cavity(48, 1e4),
+          I.rayleigh_benard(300, 70, Ra=1e5, Q=1e-4, noise=1e-2)]
+    ws[1].init = I.random_fields(48, 48, seed=17, amp=0.02)
+    ws[2].init = I.random_fields(300, 70, seed=19, amp=0.02)
+    b = clbm.Batch(ws, "f32")
+    b.solve(0.0, 300, check_every=150)
+    for i, w in enumerate(ws):
+        o = oracle.from_workload(w)
+        o.step(300)
+        errs = compare(w, b.moments(i), o.moments())
+        assert max(errs.values()) <= TOL["f32"], (w.name, errs)
+    b.close()
+
+
+@pytest.mark.parametrize("precision", ["bf16", "f16"])
+def test_batch_16bit_stochastic_against_oracle(precision):
+    """The precision of batched solves (16-bit deviation storage, stochastic
+    rounding, FP32 collision) against the FP64 oracle: the 64^2 Ra = 1e4
+    cavity, solved inside a batch for 10,000 steps beside two other lattices,
+    meets the single-lattice tolerances of the same format (field L2 of u_x,
+    u_y, T and the cold-wall Nusselt number)."""
+    from test_gpu_precision import CAVITY_TOL
+    ws = [I.natural_convection_cavity(40, 1e3), I.natural_convection_cavity(64, 1e4),
+          I.obstacle_channel()]
+    b = clbm.Batch(ws, precision, rounding=1)
+    conv, _, steps = b.solve(0.0, 10000, check_every=200)
+    assert steps == 10000 and (conv == -1).all()
+    w = ws[1]
+    o = oracle.from_workload(w)
+    o.step(10000)
+    ref = o.moments()
+    got = b.moments(1)
+    l2 = [float(np.linalg.norm(a - r) / np.linalg.norm(r)) for a, r in zip(got[1:], ref[1:])]
+    nu, nu_ref = -b.nusselt(1, 1, 64, 1.0), -o.nusselt(1, 64, 1.0)
+    tol_l2, tol_nu = CAVITY_TOL[(precision, 1)]
+    assert max(l2) < tol_l2, (precision, l2)
+    assert abs(nu - nu_ref) / abs(nu_ref) < tol_nu, (precision, nu, nu_ref)
+    b.close()
+
+
 def test_batch_convergence_and_retirement():
     """Cavities reach the tolerance at different times; each converged lattice
     stops at its own step count with its residual below tol.  (The per-step

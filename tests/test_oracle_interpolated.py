@@ -138,3 +138,36 @@ def test_annulus_interpolated_walls_beat_the_staircase():
     assert e64[1] < e64[0] / 3
     assert e64[1] < 0.5 * e32[1]
     assert e64[1] < 1.2e-3
+
+
+@pytest.mark.parametrize("N,qb,qt,top,Q", [
+    (8, 0.3, 0.8, None, 0.0),                # linear; bottom q < 1/2, top q > 1/2; Dirichlet
+    (8, 0.7, 0.2, (1.0, 0.5, 0.1), 0.0),     # linear; bottom q > 1/2, top q < 1/2; Robin top
+    (8, 0.3, 0.8, (1.0, 0.2, 0.0), 1e-3),    # parabola, Robin top (q >= 1/2)
+    (16, 0.3, 0.2, (1.0, 0.1, 0.0), 1e-3),   # parabola, Robin top (q < 1/2)
+    (8, 0.7, 0.1, None, 1e-3),               # parabola, Dirichlet, small q
+])
+def test_offset_walls_nusselt_is_the_exact_wall_flux(N, qb, qt, top, Q):
+    """The wall gradient off the link midpoint, through the Nusselt number of
+    the listed links: with walls at y_b = 1 - qb and y_t = N + qt, the steady
+    profile T = T_b + s x + Q/(2 alpha) x (L - x) (x = y - y_b) has the exact
+    outward gradients dT/dn = -(s + Q L/(2 alpha)) at the bottom wall and
+    s - Q L/(2 alpha) at the top wall.  oref_nusselt(4 + k) with length = dT = 1
+    is the mean of dT/dn over the links of condition k, so it must return these
+    fluxes (to the rounding of the steady state).  A slip in the gradient's
+    weights, in its sign or in the q used (for instance q where 1 - q belongs)
+    moves it by O(1)."""
+    nu, alpha = 0.1, 0.1
+    w = I.offset_channel(N, qb, qt, nu, alpha, 1e-5, top_tbc=top, Q=Q)
+    o = oracle.from_workload(w)
+    o.step(int(40 * (N + 1) ** 2 / alpha) + 2000)
+    ny = w.params.ny
+    yb, yt = 1.0 - qb, (ny - 2) + qt
+    L = yt - yb
+    b1, b2, b3 = w.geom.tbc[1]
+    c = Q / (2.0 * alpha)
+    s = (b3 - b2 * 1.0 + b1 * c * L) / (b1 + b2 * L)
+    assert o.nusselt(4, 1.0, 1.0) == pytest.approx(-(s + c * L), abs=1e-9)
+    assert o.nusselt(5, 1.0, 1.0) == pytest.approx(s - c * L, abs=1e-9)
+    # the fluxes are O(1/L); the tolerance is far below any formula slip
+    assert min(abs(s + c * L), abs(s - c * L)) > 1e-2 or abs(s) > 1e-2

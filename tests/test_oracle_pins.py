@@ -462,3 +462,36 @@ def test_viscous_dissipation_poiseuille_profile_and_order(paper_values):
     assert errs[1] < 1e-2
     slope = -np.polyfit(np.log(Ls), np.log(errs), 1)[0]
     assert abs(slope - paper_values["poiseuille_dissipation_slope"]["slope"]) < 0.15
+
+
+# ---------------------------------------------------------------------------
+# Steady-state residual (definition, no counterpart in the paper)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("name", ["periodic", "obstacle", "cavity"])
+def test_residual_is_the_relative_l2_change_of_T_and_u(name):
+    """oref_residual against the definition evaluated with numpy from two
+    moment snapshots one step apart: max over phi in (T, ux, uy) of
+    ||phi(t) - phi(t-1)||_2 / ||phi(t)||_2 over the fluid nodes.  The three
+    ratios differ by orders of magnitude in these cases, so the wrong norm (L1,
+    L-inf), a missing field, rho in the set, or the previous state's norm in
+    the denominator all fail; so does a residual taken over a different step."""
+    w = {"periodic": lambda: I.periodic_box(23, 17),
+         "obstacle": I.obstacle_channel,
+         "cavity": lambda: I.natural_convection_cavity(24, 1e4)}[name]()
+    o = oracle.from_workload(w)
+    o.step(7)
+    m0 = o.moments()
+    o.step(1)
+    m1 = o.moments()
+    fluid = np.ones((w.params.ny, w.params.nx), bool) if w.geom.solid is None else w.geom.solid == 0
+    ratios = []
+    for k in (3, 1, 2):  # T, ux, uy
+        a, b = m1[k][fluid], m0[k][fluid]
+        ratios.append(math.sqrt(((a - b) ** 2).sum()) / max(math.sqrt((a * a).sum()), 1e-30))
+    r = o.residual()
+    assert r == pytest.approx(max(ratios), rel=1e-12)
+    # the same change measured with other norms is far from it, so the pin
+    # distinguishes them
+    for norm in (lambda v: np.abs(v).sum(), lambda v: np.abs(v).max()):
+        alt = max(norm(m1[k][fluid] - m0[k][fluid]) / norm(m1[k][fluid]) for k in (3, 1, 2))
+        assert abs(alt - r) > 1e-3 * r

@@ -48,6 +48,40 @@ def test_noalloc_residual_matches_clbm_residual_twice(name):
     s.close()
 
 
+def test_noalloc_large_fields_against_numpy():
+    """n = 1024 x 512 > 1024 blocks x 256 threads: the grid is clamped to the
+    scratch's 1024 blocks, every thread loops over several nodes and the final
+    pass adds all 1024 partial rows.  Random fields with a random solid mask,
+    checked against the definition evaluated in FP64 with numpy, twice in a
+    row (the second call reads only what it wrote itself)."""
+    torch = pytest.importorskip("torch")
+    dev = torch.device("cuda", 0)
+    nx, ny = 1024, 512
+    n = nx * ny
+    for call in range(2):
+        r = I.splitmix64_uniform(90210 + call, 7 * n).reshape(7, n)
+        now = [0.5 + 0.3 * (2 * r[0] - 1), 0.02 * (2 * r[1] - 1), 0.02 * (2 * r[2] - 1)]
+        prev = [now[k] + 1e-4 * (2 * r[3 + k] - 1) for k in range(3)]
+        solid = (r[6] < 0.2).astype(np.uint8)
+        fluid = solid == 0
+        want = max(np.linalg.norm((a - b)[fluid]) / np.linalg.norm(a[fluid]) for a, b in zip(now, prev))
+        d = [torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in now + prev]
+        got = clbm.clbm_residual_fields_noalloc(*d, torch.from_numpy(solid).to(dev), n)
+        assert got == pytest.approx(want, rel=REL_TOL), (call, got, want)
+
+
+def test_noalloc_reports_nonfinite_values():
+    """A NaN in the current temperature: CLBM_EUNSTABLE (the binding raises)."""
+    torch = pytest.importorskip("torch")
+    n = 5000
+    a = torch.full((n,), 0.5, dtype=torch.float64, device="cuda")
+    b = a.clone()
+    b[1234] = float("nan")
+    with pytest.raises(clbm.ClbmError) as ei:
+        clbm.clbm_residual_fields_noalloc(b, a, a, a, a, a, None, n)
+    assert ei.value.status == clbm.CLBM_EUNSTABLE
+
+
 def test_noalloc_rejects_bad_sizes():
     torch = pytest.importorskip("torch")
     a = torch.zeros(4, dtype=torch.float64, device="cuda")
