@@ -193,6 +193,87 @@ clbm_status clbm_residual(clbm_ctx* ctx, double* r_out);
  * Returns CLBM_EUNSTABLE if a value is NaN or Inf.  Synchronises. */
 clbm_status clbm_totals(clbm_ctx* ctx, double* out);
 
+/* ---------------------------------------------------------------------
+ * Domain decomposition into y-slabs.  The step needs, at every node, only the
+ * post-collision populations of its eight neighbours (streaming, Eq. 11 and
+ * Eq. 21) and, at a wall link, the temperature of the next node along the
+ * link (Eq. 27-28), so a lattice splits into slabs of whole rows that each
+ * keep one ghost row on each side: after every step (and after the
+ * initialisation) each slab's first and last own rows, all planes, are copied
+ * into its neighbours' ghost rows.  A slab reproduces the whole lattice's
+ * values on its rows bit for bit.  Reductions are partial sums over the own
+ * rows (clbm_reduce_sums), added across slabs and finished with
+ * clbm_finish_sums.
+ * ------------------------------------------------------------------- */
+
+/* Create a solver for rows [y0, y0 + rows) of the lattice that `params`
+ * describes (params->ny = the whole lattice's rows, params->periodic_y its y
+ * axis).  Stores rows + 2 rows (a ghost row below and above).  Every other
+ * call takes and returns the slab's own rows: clbm_init_fields and
+ * clbm_moments arrays are [rows][nx]; clbm_set_boundaries takes the WHOLE
+ * lattice's description (solid [ny][nx], links with whole-lattice node
+ * numbers) and keeps the slab's part.  A box side y0 / y1 is a wall of the
+ * slab only if the slab holds the first / last row of a non-periodic lattice.
+ * The ghost rows start at zero: exchange halos before the first step.
+ * Errors: CLBM_EINVAL (rows < 1, y0 < 0, y0 + rows > ny, or as clbm_create);
+ * clbm_set_boundaries returns CLBM_EINVAL for an off-midpoint Dirichlet link
+ * (q < 1/2) whose third node x_f - 2 e_i lies beyond the ghost row. */
+clbm_status clbm_create_slab(const clbm_params* params, int32_t y0, int32_t rows, void* stream,
+                             clbm_ctx** out);
+
+/* Bytes of one packed halo row: planes (14, or 15 with the viscous source) x nx
+ * elements of the storage format, laid out [plane][x]. */
+clbm_status clbm_halo_bytes(const clbm_ctx* ctx, int64_t* bytes);
+
+/* Copy the slab's first (side 0) or last (side 1) own row of the current
+ * state, every plane, into the device buffer dst ([plane][x], clbm_halo_bytes
+ * bytes), on the context stream.  For exchanges through a communication
+ * library (one slab per process): side 0 goes to the slab below, side 1 to the
+ * slab above. */
+clbm_status clbm_halo_pack(clbm_ctx* ctx, int32_t side, void* dst);
+
+/* Write a packed row (device buffer, as clbm_halo_pack) into the ghost row
+ * below (side 0: the last own row of the slab below) or above (side 1: the
+ * first own row of the slab above) of the current state, on the context stream. */
+clbm_status clbm_halo_unpack(clbm_ctx* ctx, int32_t side, const void* src);
+
+/* Copy `from`'s first (side 0) or last (side 1) own row, every plane, straight
+ * into the ghost row above (side 0) or below (side 1) of `to` (the slab below /
+ * above it), with one strided copy on `to`'s stream; if the two contexts have
+ * different streams, events order the copy after `from`'s work and `from`'s
+ * later work after the copy.  Both must be slabs of the same nx, format and
+ * plane count, on one device or on peer-accessible devices. */
+clbm_status clbm_halo_copy(clbm_ctx* from, int32_t side, clbm_ctx* to);
+
+/* Exchange the halos of n slabs of one lattice held by this process, ordered
+ * bottom to top (slabs[k + 1] above slabs[k]); periodic != 0 also joins the
+ * last slab to the first. */
+clbm_status clbm_slabs_exchange(clbm_ctx* const* slabs, int32_t n, int32_t periodic);
+
+/* nsteps times: one step of every slab, then clbm_slabs_exchange. */
+clbm_status clbm_slabs_step(clbm_ctx* const* slabs, int32_t n, int32_t periodic, int64_t nsteps);
+
+/* Raw FP64 sums of one reduction over the context's own rows, into out[8]
+ * (host), for adding across slabs before clbm_finish_sums:
+ *   what = 0: residual over the last step: sum dT^2, T^2, dux^2, ux^2, duy^2,
+ *             uy^2 (differences to the previous step), non-finite count, 0;
+ *   what = 1: Nusselt selection `which` (as clbm_nusselt): sum of dT/dn over
+ *             the selection's links held here, their count (0 allowed),
+ *             non-finite count;
+ *   what = 2: conservation: sum of the stored deviations d_i, d_i e_ix,
+ *             d_i e_iy, h_j over the fluid nodes, fluid-node count,
+ *             non-finite count.
+ * Fixed-order sums; synchronises. */
+clbm_status clbm_reduce_sums(clbm_ctx* ctx, int32_t what, int32_t which, double* out);
+
+/* Finish summed reductions (the sums of every slab added element-wise):
+ * what = 0 -> out[0] = the clbm_residual value; 1 -> out[0] = the Nusselt
+ * number (length/dT x mean dT/dn); 2 -> out[0..3] = the clbm_totals values
+ * (rho0, T0 from ctx).  CLBM_EUNSTABLE for non-finite sums, CLBM_EINVAL for a
+ * Nusselt selection with no links. */
+clbm_status clbm_finish_sums(const clbm_ctx* ctx, int32_t what, const double* sums, double length,
+                             double dT, double* out);
+
 /* Allocation-free variant of the residual reduction (the paper has no
  * counterpart; it is a service for callers of this library).
  *

@@ -52,6 +52,8 @@ EXPORTS = ["clbm_create", "clbm_set_boundaries", "clbm_init_fields", "clbm_step"
            "clbm_nusselt", "clbm_residual", "clbm_totals", "clbm_residual_fields_noalloc", "clbm_batch_create",
            "clbm_batch_solve", "clbm_batch_lattice", "clbm_batch_tile_width", "clbm_batch_destroy",
            "clbm_damp_period2", "clbm_batch_damp_period2",
+           "clbm_create_slab", "clbm_halo_bytes", "clbm_halo_pack", "clbm_halo_unpack", "clbm_halo_copy",
+           "clbm_slabs_exchange", "clbm_slabs_step", "clbm_reduce_sums", "clbm_finish_sums",
            "clbm_batch_last_error", "clbm_time", "clbm_destroy", "clbm_last_error",
            "clbm_status_string"]
 
@@ -101,6 +103,15 @@ def load(path: Optional[str] = None):
     L.clbm_batch_destroy.argtypes = [vp]
     L.clbm_damp_period2.argtypes = [vp]
     L.clbm_batch_damp_period2.argtypes = [vp]
+    L.clbm_create_slab.argtypes = [C.POINTER(clbm_params), C.c_int32, C.c_int32, vp, C.POINTER(vp)]
+    L.clbm_halo_bytes.argtypes = [vp, C.POINTER(C.c_int64)]
+    L.clbm_halo_pack.argtypes = [vp, C.c_int32, vp]
+    L.clbm_halo_unpack.argtypes = [vp, C.c_int32, vp]
+    L.clbm_halo_copy.argtypes = [vp, C.c_int32, vp]
+    L.clbm_slabs_exchange.argtypes = [C.POINTER(vp), C.c_int32, C.c_int32]
+    L.clbm_slabs_step.argtypes = [C.POINTER(vp), C.c_int32, C.c_int32, C.c_int64]
+    L.clbm_reduce_sums.argtypes = [vp, C.c_int32, C.c_int32, dp]
+    L.clbm_finish_sums.argtypes = [vp, C.c_int32, dp, C.c_double, C.c_double, dp]
     L.clbm_batch_last_error.argtypes = [vp]
     L.clbm_batch_last_error.restype = C.c_char_p
     for name in EXPORTS:
@@ -220,6 +231,65 @@ def clbm_residual_fields_noalloc(T_now, ux_now, uy_now, T_prev, ux_prev, uy_prev
     return out.value
 
 
+def clbm_create_slab(params: clbm_params, y0: int, rows: int, stream: Optional[int] = None) -> C.c_void_p:
+    L = load()
+    ctx = C.c_void_p()
+    _check(L.clbm_create_slab(C.byref(params), int(y0), int(rows), stream, C.byref(ctx)), None,
+           "clbm_create_slab")
+    return ctx
+
+
+def clbm_halo_bytes(ctx) -> int:
+    out = C.c_int64()
+    _check(load().clbm_halo_bytes(ctx, C.byref(out)), ctx, "clbm_halo_bytes")
+    return out.value
+
+
+def clbm_halo_pack(ctx, side: int, dst):
+    _check(load().clbm_halo_pack(ctx, int(side), _addr(dst)), ctx, "clbm_halo_pack")
+
+
+def clbm_halo_unpack(ctx, side: int, src):
+    _check(load().clbm_halo_unpack(ctx, int(side), _addr(src)), ctx, "clbm_halo_unpack")
+
+
+def clbm_halo_copy(src_ctx, side: int, dst_ctx):
+    _check(load().clbm_halo_copy(src_ctx, int(side), dst_ctx), dst_ctx, "clbm_halo_copy")
+
+
+def _ctx_array(ctxs):
+    return (C.c_void_p * len(ctxs))(*[c.value for c in ctxs])
+
+
+def clbm_slabs_exchange(ctxs, periodic: bool):
+    _check(load().clbm_slabs_exchange(_ctx_array(ctxs), len(ctxs), int(periodic)), None,
+           "clbm_slabs_exchange")
+
+
+def clbm_slabs_step(ctxs, periodic: bool, nsteps: int):
+    _check(load().clbm_slabs_step(_ctx_array(ctxs), len(ctxs), int(periodic), int(nsteps)), None,
+           "clbm_slabs_step")
+
+
+REDUCE_RESIDUAL, REDUCE_NUSSELT, REDUCE_TOTALS = 0, 1, 2
+
+
+def clbm_reduce_sums(ctx, what: int, which: int = 0) -> np.ndarray:
+    out = np.zeros(8, np.float64)
+    _check(load().clbm_reduce_sums(ctx, int(what), int(which), out.ctypes.data_as(C.POINTER(C.c_double))),
+           ctx, "clbm_reduce_sums")
+    return out
+
+
+def clbm_finish_sums(ctx, what: int, sums, length: float = 0.0, dT: float = 1.0) -> np.ndarray:
+    h = np.ascontiguousarray(sums, np.float64)
+    out = np.zeros(4, np.float64)
+    _check(load().clbm_finish_sums(ctx, int(what), h.ctypes.data_as(C.POINTER(C.c_double)), float(length),
+                                   float(dT), out.ctypes.data_as(C.POINTER(C.c_double))), None,
+           "clbm_finish_sums")
+    return out
+
+
 def clbm_damp_period2(ctx):
     _check(load().clbm_damp_period2(ctx), ctx, "clbm_damp_period2")
 
@@ -299,6 +369,39 @@ class Solver:
     @property
     def time(self) -> int:
         return clbm_time(self.ctx)
+
+
+class Slab(Solver):
+    """Rows [y0, y0 + rows) of the lattice ``params`` describes, with a ghost
+    row on each side (``clbm_create_slab``); walls and initial fields are given
+    for the whole lattice and cut here."""
+
+    def __init__(self, params, y0: int, rows: int, geom=None, precision="f32",
+                 stream: Optional[int] = None, init=None, rounding: int = 0):
+        self.params = params
+        self.nx, self.ny = params.nx, rows
+        self.y0, self.rows = y0, rows
+        self.precision = precision
+        self.ctx = clbm_create_slab(make_params(params, precision, rounding), y0, rows, stream)
+        if geom is not None:
+            clbm_set_boundaries(self.ctx, geom.solid, geom.tbc, geom.side_tbc, geom.link_node,
+                                geom.link_dir, geom.link_ne, geom.link_tbc, geom.link_q_or_half())
+        if init is not None:
+            self.init(init)
+
+    def init(self, fields=None):
+        if fields is None:
+            clbm_init_fields(self.ctx)
+            return
+        full = (self.params.ny, self.nx)
+        arrs = []
+        for a in (fields.rho, fields.ux, fields.uy, fields.T):
+            arrs.append(None if a is None else
+                        np.ascontiguousarray(np.broadcast_to(a, full)[self.y0:self.y0 + self.rows], np.float64))
+        clbm_init_fields(self.ctx, *arrs)
+
+    def sums(self, what: int, which: int = 0) -> np.ndarray:
+        return clbm_reduce_sums(self.ctx, what, which)
 
 
 def from_workload(w, precision="f32", stream=None, rounding: int = 0) -> Solver:

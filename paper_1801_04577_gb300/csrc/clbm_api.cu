@@ -44,6 +44,13 @@ struct clbm_ctx {
   bool own_stream = false;
   void* buf[2] = {nullptr, nullptr};
   bool borrowed = false;  // buffers owned by a batch arena
+  // y-slab of a larger lattice: p.ny = stored rows (own rows + one ghost row on
+  // each side), p.periodic_y = 0; gny / gpy describe the whole lattice and the
+  // own rows [ylo, yhi) hold its rows y0 .. y0 + (yhi - ylo) - 1
+  bool slab = false;
+  int gny = 0, gpy = 0, y0 = 0;
+  int ylo = 0, yhi = 0, ywlo = 0, ywhi = 0;
+  cudaEvent_t ev_halo[2] = {nullptr, nullptr};  // orders halo copies between two streams
   int cur = 0;
   int64_t t = 0;
   bool have_walls = false;
@@ -58,9 +65,9 @@ struct clbm_ctx {
   double* d_tbc = nullptr;
   std::vector<int32_t> h_bnodes;  // nodes the boundary kernel recomputes (pitch layout)
   int32_t* d_bnodes = nullptr;
-  std::vector<uint8_t> h_solid;
+  std::vector<uint8_t> h_solid;    // [p.ny][nx] over the stored rows (empty: no mask)
   std::vector<clbm_tbc> h_tbc;
-  std::vector<clbm_link> h_links;
+  std::vector<clbm_link> h_links;  // links of own-row nodes, node = stored row * nx + x
   int side_tbc[4] = {-1, -1, -1, -1};
   double side_b[4][3] = {};
   // scratch
@@ -116,6 +123,11 @@ static DevGeom make_geom(const clbm_ctx* c) {
   g.pitch = c->pitch;
   g.px = c->p.periodic_x ? 1 : 0;
   g.py = c->p.periodic_y ? 1 : 0;
+  g.ylo = c->ylo;
+  g.yhi = c->yhi;
+  g.ywlo = c->ywlo;
+  g.ywhi = c->ywhi;
+  g.yoff = c->slab ? c->y0 - 1 : 0;
   g.plane = c->plane;
   g.flags = c->d_flags;
   g.slot = c->d_slot;
@@ -181,12 +193,11 @@ static void free_tables(clbm_ctx* c) {
 // y axis, and (masked lattices) every fluid node with a wall or solid among
 // its pull sources.  Solid nodes are never listed.
 static cudaError_t upload_boundary_list(clbm_ctx* c, const std::vector<uint16_t>& flags) {
-  const int nx = c->p.nx, ny = c->p.ny;
-  const bool py = c->p.periodic_y;
+  const int nx = c->p.nx;
   std::vector<int32_t>& v = c->h_bnodes;
   v.clear();
-  for (int y = 0; y < ny; ++y) {
-    const bool yedge = !py && (y == 0 || y == ny - 1);
+  for (int y = c->ylo; y < c->yhi; ++y) {  // own rows only (ghost rows are never updated)
+    const bool yedge = (c->ywlo && y == c->ylo) || (c->ywhi && y == c->yhi - 1);
     for (int x = 0; x < nx; ++x) {
       const size_t ip = (size_t)y * c->pitch + x;
       bool need = yedge || x == 0 || x == nx - 1;
@@ -234,17 +245,31 @@ clbm_status clbm_destroy(clbm_ctx* c) {
   }
   cudaFree(c->d_fields);
   cudaFree(c->d_part);
+  for (auto& e : c->ev_halo)
+    if (e) cudaEventDestroy(e);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   delete c;
   return CLBM_OK;
 }
 
+// A y-slab: rows [y0, y0 + rows) of the lattice `params` describes.
+struct SlabSpec {
+  int y0, rows;
+};
+
 static clbm_status create_impl(const clbm_params* params, void* stream, void* buf_a, void* buf_b,
-                               clbm_ctx** out) {
+                               clbm_ctx** out, const SlabSpec* slab = nullptr) {
   if (!out) return CLBM_EINVAL;
   *out = nullptr;
   if (!params) return CLBM_EINVAL;
-  const clbm_params& p = *params;
+  clbm_params pl = *params;
+  if (slab) {  // store the own rows plus a ghost row on each side
+    if (pl.ny < 1 || slab->rows < 1 || slab->y0 < 0 || (long long)slab->y0 + slab->rows > pl.ny)
+      return CLBM_EINVAL;
+    pl.ny = slab->rows + 2;
+    pl.periodic_y = 0;
+  }
+  const clbm_params& p = pl;
   const Launchers* L = launchers_for(p.precision);
   if (!L) return CLBM_EINVAL;
   if (p.nx < 1 || p.ny < 1 || p.ny > 65535 || (long long)p.nx * p.ny > (1LL << 31))
@@ -258,6 +283,22 @@ static clbm_status create_impl(const clbm_params* params, void* stream, void* bu
   clbm_ctx* c = new (std::nothrow) clbm_ctx();
   if (!c) return CLBM_ENOMEM;
   c->p = p;
+  if (slab) {
+    c->slab = true;
+    c->gny = params->ny;
+    c->gpy = params->periodic_y ? 1 : 0;
+    c->y0 = slab->y0;
+    c->ylo = 1;
+    c->yhi = 1 + slab->rows;
+    c->ywlo = !c->gpy && slab->y0 == 0;
+    c->ywhi = !c->gpy && slab->y0 + slab->rows == params->ny;
+  } else {
+    c->gny = p.ny;
+    c->gpy = p.periodic_y ? 1 : 0;
+    c->ylo = 0;
+    c->yhi = p.ny;
+    c->ywlo = c->ywhi = p.periodic_y ? 0 : 1;
+  }
   c->s3 = p.s_3 > 0 ? p.s_3 : (16.0 - 8.0 * p.s_nu) / (8.0 - p.s_nu);
   c->l2 = p.lambda2 > 0 ? p.lambda2 : 12.0 * (p.lambda1 - 2.0) / (p.lambda1 - 12.0);
   if (!rate_ok(c->s3) || !rate_ok(c->l2)) {
@@ -268,7 +309,7 @@ static clbm_status create_impl(const clbm_params* params, void* stream, void* bu
   c->pitch = view_pitch(p.nx, p.precision);
   c->plane = (long long)p.ny * c->pitch;
   c->buf_bytes = (size_t)planes_of(p.viscous_heating) * (size_t)c->plane * L->elem_bytes;
-  c->have_walls = p.periodic_x && p.periodic_y;
+  c->have_walls = p.periodic_x && c->gpy;
   for (int s = 0; s < 4; ++s)
     for (int k = 0; k < 3; ++k) c->side_b[s][k] = 0.0;
   cudaError_t e;
@@ -331,8 +372,11 @@ clbm_status clbm_set_boundaries(clbm_ctx* c, const uint8_t* solid, const clbm_tb
                                 int32_t n_links) {
   if (!c) return CLBM_EINVAL;
   try {
-    const int nx = c->p.nx, ny = c->p.ny;
-    const bool px = c->p.periodic_x, py = c->p.periodic_y;
+    // The caller describes the whole lattice (NY rows).  A slab stores rows
+    // r = 0 .. ny - 1 holding the lattice's rows y0 - 1 + r (own rows
+    // [ylo, yhi), ghost rows around them); a whole lattice stores every row.
+    const int nx = c->p.nx, ny = c->p.ny, NY = c->gny;
+    const bool px = c->p.periodic_x, gpy = c->gpy;
     if (n_tbc < 0 || n_links < 0 || (n_tbc > 0 && !tbc) || (n_links > 0 && !links))
       return fail(c, CLBM_EINVAL, "null table with a positive count");
     for (int k = 0; k < n_tbc; ++k) {
@@ -344,32 +388,59 @@ clbm_status clbm_set_boundaries(clbm_ctx* c, const uint8_t* solid, const clbm_tb
     }
     int sides[4];
     for (int s = 0; s < 4; ++s) {
-      const bool periodic = s < 2 ? px : py;
+      const bool periodic = s < 2 ? px : gpy;
       sides[s] = side_tbc ? side_tbc[s] : -1;
       if (!periodic && (sides[s] < 0 || sides[s] >= n_tbc))
         return fail(c, CLBM_EINVAL, "box side " + std::to_string(s) + " needs a thermal condition");
       if (periodic) sides[s] = -1;
     }
-    const long long n = (long long)nx * ny;
-    std::vector<uint8_t> sol;
-    if (solid) sol.assign(solid, solid + n);
+    const long long n = (long long)nx * NY;
+    // lattice row of stored row r (-1: beyond a box wall, not part of the lattice)
+    auto grow = [&](int r) -> int {
+      if (!c->slab) return r;
+      int gy = c->y0 - 1 + r;
+      if (gy < 0 || gy >= NY) {
+        if (!gpy) return -1;
+        gy = (gy + NY) % NY;
+      }
+      return gy;
+    };
+    std::vector<uint8_t> sol;  // [ny][nx] over the stored rows
+    if (solid) {
+      sol.assign((size_t)ny * nx, 0);
+      for (int r = 0; r < ny; ++r) {
+        const int gy = grow(r);
+        if (gy >= 0) std::memcpy(&sol[(size_t)r * nx], solid + (size_t)gy * nx, (size_t)nx);
+      }
+    }
     auto is_solid = [&](int x, int y) { return !sol.empty() && sol[(size_t)y * nx + x] != 0; };
-    // listed links: per node a slot with 4 directions
+    // listed links of own-row nodes: per node a slot with 4 directions
     std::vector<int32_t> slot_of;  // dense [ny][nx]
     std::vector<double> lk_ne;
     std::vector<int32_t> lk_tbc;
     std::vector<double> lk_q;  // 8 per slot
-    const bool masked = !sol.empty() || n_links > 0;
-    if (masked) slot_of.assign((size_t)n, -1);
+    std::vector<clbm_link> kept;
+    const bool masked = solid != nullptr || n_links > 0;
+    if (masked) slot_of.assign((size_t)ny * nx, -1);
     for (int l = 0; l < n_links; ++l) {
       const clbm_link& k = links[l];
       const bool axis = k.dir >= 1 && k.dir <= 4;
       if (k.node < 0 || k.node >= n || k.dir < 1 || k.dir > 8 || !(k.q > 0.0 && k.q <= 1.0) ||
           (axis && (k.tbc < 0 || k.tbc >= n_tbc || !(k.n_dot_e > 0) || !std::isfinite(k.n_dot_e))))
         return fail(c, CLBM_EINVAL, "bad wall link " + std::to_string(l));
-      const int x = (int)(k.node % nx), y = (int)(k.node / nx);
-      if (is_solid(x, y)) return fail(c, CLBM_EINVAL, "wall link from a solid node");
-      int32_t& s = slot_of[(size_t)k.node];
+      const int x = (int)(k.node % nx), gy = (int)(k.node / nx);
+      if (solid && solid[k.node]) return fail(c, CLBM_EINVAL, "wall link from a solid node");
+      const int y = gy - c->y0 + c->ylo;  // stored row (whole lattices: y0 = ylo = 0)
+      if (y < c->ylo || y >= c->yhi) continue;  // another slab's node
+      if (c->slab && axis && k.q < 0.5 && tbc[k.tbc].b1 == 0.0) {
+        // the off-midpoint Dirichlet rule reads T at x_f - 2 e_i: it must be stored
+        const int y3 = y + 2 * kEY[k.dir];
+        const int gy3 = gy + 2 * kEY[k.dir];
+        if ((y3 < 0 || y3 >= ny) && (gpy || (gy3 >= 0 && gy3 < NY)))
+          return fail(c, CLBM_EINVAL, "slab too thin for wall link " + std::to_string(l) +
+                                          ": its third node lies beyond the ghost row");
+      }
+      int32_t& s = slot_of[(size_t)y * nx + x];
       if (s < 0) {
         s = (int32_t)(lk_tbc.size() / 4);
         lk_ne.insert(lk_ne.end(), 4, 0.0);
@@ -381,6 +452,9 @@ clbm_status clbm_set_boundaries(clbm_ctx* c, const uint8_t* solid, const clbm_tb
         lk_tbc[4 * s + k.dir - 1] = k.tbc;
       }
       lk_q[8 * s + k.dir - 1] = k.q;
+      clbm_link kk = k;
+      kk.node = y * nx + x;
+      kept.push_back(kk);
     }
     std::vector<uint16_t> flags;
     std::vector<int32_t> slot_pitch;
@@ -394,6 +468,7 @@ clbm_status clbm_set_boundaries(clbm_ctx* c, const uint8_t* solid, const clbm_tb
             flags[ip] = kFlagSolid;
             continue;
           }
+          if (y < c->ylo || y >= c->yhi) continue;  // ghost rows: only their solid bits are read
           uint16_t f = 0;
           int fluid_nb = 0;
           for (int j = 1; j < 9; ++j) {
@@ -402,8 +477,11 @@ clbm_status clbm_set_boundaries(clbm_ctx* c, const uint8_t* solid, const clbm_tb
             if (sx < 0 || sx >= nx) {
               if (px) sx = (sx + nx) % nx; else wall = true;
             }
-            if (sy < 0 || sy >= ny) {
-              if (py) sy = (sy + ny) % ny; else wall = true;
+            if (sy < c->ylo || sy >= c->yhi) {
+              if (sy < c->ylo ? c->ywlo : c->ywhi)
+                wall = true;
+              else if (!c->slab)
+                sy = (sy + ny) % ny;  // periodic seam (slabs read their ghost row)
             }
             if (!wall && is_solid(sx, sy)) {
               wall = true;
@@ -412,7 +490,7 @@ clbm_status clbm_set_boundaries(clbm_ctx* c, const uint8_t* solid, const clbm_tb
                 const int s = slot_of[(size_t)y * nx + x];
                 if (s < 0 || lk_tbc[4 * s + kOpp[j] - 1] < 0)
                   return fail(c, CLBM_EINVAL, "missing wall link at node " +
-                                                  std::to_string((long long)y * nx + x) +
+                                                  std::to_string((long long)grow(y) * nx + x) +
                                                   " dir " + std::to_string(kOpp[j]));
               }
             }
@@ -420,7 +498,7 @@ clbm_status clbm_set_boundaries(clbm_ctx* c, const uint8_t* solid, const clbm_tb
             else ++fluid_nb;
           }
           if (fluid_nb == 0 && n > 1)
-            return fail(c, CLBM_EINVAL, "isolated fluid node " + std::to_string((long long)y * nx + x));
+            return fail(c, CLBM_EINVAL, "isolated fluid node " + std::to_string((long long)grow(y) * nx + x));
           const int s = slot_of[(size_t)y * nx + x];
           if (s >= 0) {
             f |= kFlagLinks;
@@ -487,7 +565,7 @@ clbm_status clbm_set_boundaries(clbm_ctx* c, const uint8_t* solid, const clbm_tb
     }
     c->h_solid = std::move(sol);
     c->h_tbc.assign(tbc, tbc + n_tbc);
-    c->h_links.assign(links, links + n_links);
+    c->h_links = std::move(kept);
     c->have_walls = true;
     return CLBM_OK;
   } catch (const std::bad_alloc&) {
@@ -499,7 +577,7 @@ clbm_status clbm_set_boundaries(clbm_ctx* c, const uint8_t* solid, const clbm_tb
 
 static clbm_status ensure_fields_scratch(clbm_ctx* c) {
   if (c->d_fields) return CLBM_OK;
-  const size_t n = (size_t)c->p.nx * c->p.ny;
+  const size_t n = (size_t)c->p.nx * (c->yhi - c->ylo);
   cudaError_t e = cudaMalloc(&c->d_fields, 4 * n * sizeof(double));
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -512,7 +590,7 @@ static clbm_status ensure_fields_scratch(clbm_ctx* c) {
 clbm_status clbm_init_fields(clbm_ctx* c, const double* rho, const double* ux, const double* uy,
                              const double* T, int32_t on_device) {
   if (!c) return CLBM_EINVAL;
-  const size_t n = (size_t)c->p.nx * c->p.ny;
+  const size_t n = (size_t)c->p.nx * (c->yhi - c->ylo);
   const double* src[4] = {rho, ux, uy, T};
   const double* dev[4] = {nullptr, nullptr, nullptr, nullptr};
   if (on_device) {
@@ -618,6 +696,97 @@ clbm_status clbm_step(clbm_ctx* c, int64_t nsteps) {
   return CLBM_OK;
 }
 
+clbm_status clbm_create_slab(const clbm_params* params, int32_t y0, int32_t rows, void* stream,
+                             clbm_ctx** out) {
+  SlabSpec sp{y0, rows};
+  return create_impl(params, stream, nullptr, nullptr, out, &sp);
+}
+
+static int plane_count(const clbm_ctx* c) { return planes_of(c->p.viscous_heating); }
+
+clbm_status clbm_halo_bytes(const clbm_ctx* c, int64_t* bytes) {
+  if (!c || !bytes) return CLBM_EINVAL;
+  *bytes = (int64_t)plane_count(c) * c->p.nx * (int64_t)c->L->elem_bytes;
+  return CLBM_OK;
+}
+
+// One row of every plane of the current state: row `row` of buffer `buf`.
+static char* row_ptr(const clbm_ctx* c, int row) {
+  return static_cast<char*>(c->buf[c->cur]) + (size_t)row * c->pitch * c->L->elem_bytes;
+}
+
+clbm_status clbm_halo_pack(clbm_ctx* c, int32_t side, void* dst) {
+  if (!c || !dst || (side != 0 && side != 1) || !c->slab) return fail(c, CLBM_EINVAL, "bad halo pack");
+  const size_t eb = c->L->elem_bytes, w = (size_t)c->p.nx * eb;
+  CLBM_CUDA(c, cudaMemcpy2DAsync(dst, w, row_ptr(c, side ? c->yhi - 1 : c->ylo), c->plane * eb, w,
+                                 plane_count(c), cudaMemcpyDeviceToDevice, c->stream));
+  return CLBM_OK;
+}
+
+clbm_status clbm_halo_unpack(clbm_ctx* c, int32_t side, const void* src) {
+  if (!c || !src || (side != 0 && side != 1) || !c->slab) return fail(c, CLBM_EINVAL, "bad halo unpack");
+  const size_t eb = c->L->elem_bytes, w = (size_t)c->p.nx * eb;
+  CLBM_CUDA(c, cudaMemcpy2DAsync(row_ptr(c, side ? c->yhi : c->ylo - 1), c->plane * eb, src, w, w,
+                                 plane_count(c), cudaMemcpyDeviceToDevice, c->stream));
+  return CLBM_OK;
+}
+
+clbm_status clbm_halo_copy(clbm_ctx* from, int32_t side, clbm_ctx* to) {
+  if (!from || !to || (side != 0 && side != 1) || !from->slab || !to->slab)
+    return fail(to, CLBM_EINVAL, "bad halo copy");
+  if (from->p.nx != to->p.nx || from->L != to->L || plane_count(from) != plane_count(to))
+    return fail(to, CLBM_EINVAL, "halo copy between different lattices");
+  const size_t eb = from->L->elem_bytes, w = (size_t)from->p.nx * eb;
+  const bool two = from->stream != to->stream;
+  if (two) {  // the copy waits for `from`'s step; `from`'s next writes wait for the copy
+    for (clbm_ctx* k : {from, to})
+      if (!k->ev_halo[0]) {
+        CLBM_CUDA(to, cudaEventCreateWithFlags(&k->ev_halo[0], cudaEventDisableTiming));
+        CLBM_CUDA(to, cudaEventCreateWithFlags(&k->ev_halo[1], cudaEventDisableTiming));
+      }
+    CLBM_CUDA(to, cudaEventRecord(from->ev_halo[0], from->stream));
+    CLBM_CUDA(to, cudaStreamWaitEvent(to->stream, from->ev_halo[0], 0));
+  }
+  // side 0: `from`'s first own row -> the ghost row above `to` (the slab below);
+  // side 1: its last own row -> the ghost row below `to` (the slab above)
+  CLBM_CUDA(to, cudaMemcpy2DAsync(row_ptr(to, side ? to->ylo - 1 : to->yhi), to->plane * eb,
+                                  row_ptr(from, side ? from->yhi - 1 : from->ylo), from->plane * eb, w,
+                                  plane_count(from), cudaMemcpyDefault, to->stream));
+  if (two) {
+    CLBM_CUDA(to, cudaEventRecord(to->ev_halo[1], to->stream));
+    CLBM_CUDA(to, cudaStreamWaitEvent(from->stream, to->ev_halo[1], 0));
+  }
+  return CLBM_OK;
+}
+
+clbm_status clbm_slabs_exchange(clbm_ctx* const* slabs, int32_t n, int32_t periodic) {
+  if (!slabs || n < 1) return CLBM_EINVAL;
+  for (int k = 0; k < n; ++k)
+    if (!slabs[k] || !slabs[k]->slab) return CLBM_EINVAL;
+  for (int k = 0; k < n; ++k) {
+    const int up = k + 1 < n ? k + 1 : (periodic ? 0 : -1);
+    if (up < 0) continue;
+    clbm_status st = clbm_halo_copy(slabs[k], 1, slabs[up]);  // k's top row below `up`
+    if (st != CLBM_OK) return st;
+    st = clbm_halo_copy(slabs[up], 0, slabs[k]);  // `up`'s bottom row above k
+    if (st != CLBM_OK) return st;
+  }
+  return CLBM_OK;
+}
+
+clbm_status clbm_slabs_step(clbm_ctx* const* slabs, int32_t n, int32_t periodic, int64_t nsteps) {
+  if (!slabs || n < 1 || nsteps < 0) return CLBM_EINVAL;
+  for (int64_t s = 0; s < nsteps; ++s) {
+    for (int k = 0; k < n; ++k) {
+      clbm_status st = clbm_step(slabs[k], 1);
+      if (st != CLBM_OK) return st;
+    }
+    clbm_status st = clbm_slabs_exchange(slabs, n, periodic);
+    if (st != CLBM_OK) return st;
+  }
+  return CLBM_OK;
+}
+
 clbm_status clbm_damp_period2(clbm_ctx* c) {
   if (!c) return CLBM_EINVAL;
   if (c->t < 1) return fail(c, CLBM_EINVAL, "needs one step after initialisation");
@@ -635,7 +804,7 @@ clbm_status clbm_time(const clbm_ctx* c, int64_t* t_out) {
 clbm_status clbm_moments(clbm_ctx* c, double* rho, double* ux, double* uy, double* T,
                          int32_t on_device) {
   if (!c) return CLBM_EINVAL;
-  const size_t n = (size_t)c->p.nx * c->p.ny;
+  const size_t n = (size_t)c->p.nx * (c->yhi - c->ylo);
   if (on_device) {
     CLBM_CUDA(c, c->L->moments(make_geom(c), make_coef(c), c->buf[c->cur], rho, ux, uy, T, c->stream));
     return CLBM_OK;
@@ -658,141 +827,208 @@ static int red_blocks(long long work) {
   return (int)std::max(1LL, std::min<long long>(b, kMaxRedBlocks));
 }
 
-clbm_status clbm_nusselt(clbm_ctx* c, int32_t which, double length, double dT, double* nu_out) {
-  if (!c || !nu_out || which < 0 || !(dT != 0) || !std::isfinite(length))
-    return fail(c, CLBM_EINVAL, "bad Nusselt arguments");
-  if (!c->have_walls) return fail(c, CLBM_EINVAL, "no walls");
-  try {
-    auto it = c->nu_lists.find(which);
-    if (it == c->nu_lists.end()) {
-      const int nx = c->p.nx, ny = c->p.ny, pitch = c->pitch;
-      const bool px = c->p.periodic_x, py = c->p.periodic_y;
-      auto solid = [&](int x, int y) { return !c->h_solid.empty() && c->h_solid[(size_t)y * nx + x]; };
-      auto second = [&](int x, int y, int dx, int dy) -> long long {
-        int x2 = x + dx, y2 = y + dy;
-        if (x2 < 0 || x2 >= nx) {
-          if (!px) return -1;
-          x2 = (x2 + nx) % nx;
-        }
-        if (y2 < 0 || y2 >= ny) {
-          if (!py) return -1;
-          y2 = (y2 + ny) % ny;
-        }
-        if (solid(x2, y2)) return -1;
-        return (long long)y2 * pitch + x2;
-      };
-      std::vector<NuLink> v;
-      if (which < 4) {
-        if (c->side_tbc[which] < 0) return fail(c, CLBM_EINVAL, "periodic side has no wall");
-        const clbm_tbc& b = c->h_tbc[c->side_tbc[which]];
-        // link direction i toward the wall: x0 -> 3, x1 -> 1, y0 -> 4, y1 -> 2
-        const int i = which == 0 ? 3 : which == 1 ? 1 : which == 2 ? 4 : 2;
-        const int cnt = which < 2 ? ny : nx;
-        for (int k = 0; k < cnt; ++k) {
-          const int x = which == 0 ? 0 : which == 1 ? nx - 1 : k;
-          const int y = which == 2 ? 0 : which == 3 ? ny - 1 : (which < 2 ? k : 0);
-          if (solid(x, y)) continue;
-          NuLink L;
-          L.own = (long long)y * pitch + x;
-          L.second = second(x, y, -kEX[i], -kEY[i]);
-          L.ne = 1.0;
-          L.b1 = b.b1;
-          L.b2 = b.b2;
-          L.b3 = b.b3;
-          L.q = 0.5;
-          v.push_back(L);
-        }
-      } else {
-        const int t = which - 4;
-        for (const clbm_link& k : c->h_links) {
-          if (k.dir > 4 || k.tbc != t) continue;  // diagonal links carry only q
-          const int x = (int)(k.node % nx), y = (int)(k.node / nx);
-          const clbm_tbc& b = c->h_tbc[t];
-          NuLink L;
-          L.own = (long long)y * pitch + x;
-          L.second = second(x, y, -kEX[k.dir], -kEY[k.dir]);
-          L.ne = k.n_dot_e;
-          L.b1 = b.b1;
-          L.b2 = b.b2;
-          L.b3 = b.b3;
-          L.q = k.q;
-          v.push_back(L);
-        }
+// The Nusselt link list of a selection (built on the host once, then cached):
+// which = 0..3 a box side, 4 + k the listed links with condition k.  A slab
+// lists only its own nodes' links (none for a box side it does not touch).
+static clbm_status nusselt_list(clbm_ctx* c, int which, const NuLink** out, int* count) {
+  auto it = c->nu_lists.find(which);
+  if (it == c->nu_lists.end()) {
+    const int nx = c->p.nx, pitch = c->pitch;
+    const bool px = c->p.periodic_x;
+    auto solid = [&](int x, int y) { return !c->h_solid.empty() && c->h_solid[(size_t)y * nx + x]; };
+    auto second = [&](int x, int y, int dx, int dy) -> long long {
+      int x2 = x + dx, y2 = y + dy;
+      if (x2 < 0 || x2 >= nx) {
+        if (!px) return -1;
+        x2 = (x2 + nx) % nx;
       }
-      if (v.empty()) return fail(c, CLBM_EINVAL, "selection has no wall links");
-      NuLink* d = nullptr;
+      if (y2 < c->ylo || y2 >= c->yhi) {
+        if (y2 < c->ylo ? c->ywlo : c->ywhi) return -1;  // beyond a box wall
+        if (!c->slab) y2 = (y2 + c->p.ny) % c->p.ny;     // periodic seam (slabs: ghost row)
+      }
+      if (solid(x2, y2)) return -1;
+      return (long long)y2 * pitch + x2;
+    };
+    std::vector<NuLink> v;
+    if (which < 4) {
+      if (c->side_tbc[which] < 0) return fail(c, CLBM_EINVAL, "periodic side has no wall");
+      const clbm_tbc& b = c->h_tbc[c->side_tbc[which]];
+      // link direction i toward the wall: x0 -> 3, x1 -> 1, y0 -> 4, y1 -> 2
+      const int i = which == 0 ? 3 : which == 1 ? 1 : which == 2 ? 4 : 2;
+      const bool here = which < 2 || (which == 2 ? c->ywlo : c->ywhi);
+      const int cnt = !here ? 0 : (which < 2 ? c->yhi - c->ylo : nx);
+      for (int k = 0; k < cnt; ++k) {
+        const int x = which == 0 ? 0 : which == 1 ? nx - 1 : k;
+        const int y = which == 2 ? c->ylo : which == 3 ? c->yhi - 1 : c->ylo + k;
+        if (solid(x, y)) continue;
+        NuLink L;
+        L.own = (long long)y * pitch + x;
+        L.second = second(x, y, -kEX[i], -kEY[i]);
+        L.ne = 1.0;
+        L.b1 = b.b1;
+        L.b2 = b.b2;
+        L.b3 = b.b3;
+        L.q = 0.5;
+        v.push_back(L);
+      }
+    } else {
+      const int t = which - 4;
+      if (t >= (int)c->h_tbc.size()) return fail(c, CLBM_EINVAL, "no such thermal condition");
+      for (const clbm_link& k : c->h_links) {
+        if (k.dir > 4 || k.tbc != t) continue;  // diagonal links carry only q
+        const int x = (int)(k.node % nx), y = (int)(k.node / nx);
+        const clbm_tbc& b = c->h_tbc[t];
+        NuLink L;
+        L.own = (long long)y * pitch + x;
+        L.second = second(x, y, -kEX[k.dir], -kEY[k.dir]);
+        L.ne = k.n_dot_e;
+        L.b1 = b.b1;
+        L.b2 = b.b2;
+        L.b3 = b.b3;
+        L.q = k.q;
+        v.push_back(L);
+      }
+    }
+    NuLink* d = nullptr;
+    if (!v.empty()) {
       CLBM_CUDA(c, cudaMalloc(&d, v.size() * sizeof(NuLink)));
       cudaError_t e = cudaMemcpy(d, v.data(), v.size() * sizeof(NuLink), cudaMemcpyHostToDevice);
       if (e != cudaSuccess) {
         cudaFree(d);
         return cuda_fail(c, e, "upload Nusselt links");
       }
-      it = c->nu_lists.emplace(which, std::make_pair(d, (int)v.size())).first;
     }
-    const int nl = it->second.second;
+    it = c->nu_lists.emplace(which, std::make_pair(d, (int)v.size())).first;
+  }
+  *out = it->second.first;
+  *count = it->second.second;
+  return CLBM_OK;
+}
+
+// Raw FP64 sums of one reduction over the own rows (the residual, Nusselt and
+// conservation entry points finish these; slabs of one lattice add theirs first).
+static clbm_status reduce_sums(clbm_ctx* c, int what, int which, double* out) {
+  double* red = c->d_part + kMaxRedBlocks * 8;
+  int width = 8;
+  if (what == 0) {  // residual: dT^2, T^2, dux^2, ux^2, duy^2, uy^2, non-finite count
+    if (c->t < 1) return fail(c, CLBM_EINVAL, "residual needs one step after initialisation");
+    const int nb = red_blocks((long long)c->p.nx * (c->yhi - c->ylo));
+    CLBM_CUDA(c, c->L->residual(make_geom(c), make_coef(c), c->buf[c->cur], c->buf[c->cur ^ 1],
+                                c->d_part, nb, c->stream));
+    CLBM_CUDA(c, launch_reduce_partials(c->d_part, nb, 8, red, c->stream));
+  } else if (what == 1) {  // Nusselt: sum of dT/dn, link count, non-finite count
+    if (!c->have_walls) return fail(c, CLBM_EINVAL, "no walls");
+    const NuLink* links = nullptr;
+    int nl = 0;
+    clbm_status st = nusselt_list(c, which, &links, &nl);
+    if (st != CLBM_OK) return st;
+    for (int k = 0; k < 8; ++k) out[k] = 0.0;
+    if (nl == 0) return CLBM_OK;
     const int nb = red_blocks(nl);
-    double* out = c->d_part + kMaxRedBlocks * 8;
-    CLBM_CUDA(c, c->L->nusselt(make_geom(c), make_coef(c), c->buf[c->cur], it->second.first, nl,
-                               c->d_part, nb, c->stream));
-    CLBM_CUDA(c, launch_reduce_partials(c->d_part, nb, 2, out, c->stream));
+    CLBM_CUDA(c, c->L->nusselt(make_geom(c), make_coef(c), c->buf[c->cur], links, nl, c->d_part, nb,
+                               c->stream));
+    CLBM_CUDA(c, launch_reduce_partials(c->d_part, nb, 2, red, c->stream));
     double h[2];
-    CLBM_CUDA(c, cudaMemcpyAsync(h, out, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+    CLBM_CUDA(c, cudaMemcpyAsync(h, red, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
     CLBM_CUDA(c, cudaStreamSynchronize(c->stream));
-    if (h[1] != 0.0) {
-      *nu_out = NAN;
-      return fail(c, CLBM_EUNSTABLE, "non-finite wall gradient");
-    }
-    *nu_out = length / dT * (h[0] / (double)nl);
+    out[0] = h[0];
+    out[1] = (double)nl;
+    out[2] = h[1];
     return CLBM_OK;
+  } else if (what == 2) {  // totals: sum d_i, d_i e_ix, d_i e_iy, h_j, fluid count, non-finite count
+    const int nb = red_blocks((long long)c->p.nx * (c->yhi - c->ylo));
+    CLBM_CUDA(c, c->L->totals(make_geom(c), c->buf[c->cur], c->d_part, nb, c->stream));
+    CLBM_CUDA(c, launch_reduce_partials(c->d_part, nb, 8, red, c->stream));
+  } else {
+    return fail(c, CLBM_EINVAL, "unknown reduction");
+  }
+  CLBM_CUDA(c, cudaMemcpyAsync(out, red, width * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CLBM_CUDA(c, cudaStreamSynchronize(c->stream));
+  return CLBM_OK;
+}
+
+static clbm_status finish_sums(const clbm_ctx* c, int what, const double* h, double length,
+                               double dT, double* out) {
+  if (what == 0) {
+    if (h[6] != 0.0 || !std::isfinite(h[0] + h[1] + h[2] + h[3] + h[4] + h[5])) {
+      out[0] = INFINITY;
+      return CLBM_EUNSTABLE;
+    }
+    double best = 0.0;
+    for (int k = 0; k < 3; ++k) {
+      const double v = std::sqrt(h[2 * k]) / std::max(std::sqrt(h[2 * k + 1]), 1e-30);
+      best = std::max(best, v);
+    }
+    out[0] = best;
+    return CLBM_OK;
+  }
+  if (what == 1) {
+    if (!(h[1] > 0)) return CLBM_EINVAL;
+    if (h[2] != 0.0) {
+      out[0] = NAN;
+      return CLBM_EUNSTABLE;
+    }
+    out[0] = length / dT * (h[0] / h[1]);
+    return CLBM_OK;
+  }
+  if (what == 2) {
+    // the stored values are deviations from the rest state: f_i = w_i rho0 + d_i,
+    // g_j = w_j T0 + h_j (the rest state carries no momentum)
+    out[0] = h[4] * c->p.rho0 + h[0];
+    out[1] = h[1];
+    out[2] = h[2];
+    out[3] = h[4] * c->p.T0 + h[3];
+    if (h[5] != 0.0 || !std::isfinite(out[0] + out[1] + out[2] + out[3])) return CLBM_EUNSTABLE;
+    return CLBM_OK;
+  }
+  return CLBM_EINVAL;
+}
+
+clbm_status clbm_reduce_sums(clbm_ctx* c, int32_t what, int32_t which, double* out) {
+  if (!c || !out) return fail(c, CLBM_EINVAL, "bad reduction arguments");
+  try {
+    return reduce_sums(c, what, which, out);
   } catch (const std::bad_alloc&) {
     return fail(c, CLBM_ENOMEM, "host allocation failed");
   }
 }
 
+clbm_status clbm_finish_sums(const clbm_ctx* c, int32_t what, const double* sums, double length,
+                             double dT, double* out) {
+  if (!c || !sums || !out || (what == 1 && !(dT != 0)) || !std::isfinite(length)) return CLBM_EINVAL;
+  return finish_sums(c, what, sums, length, dT, out);
+}
+
+clbm_status clbm_nusselt(clbm_ctx* c, int32_t which, double length, double dT, double* nu_out) {
+  if (!c || !nu_out || which < 0 || !(dT != 0) || !std::isfinite(length))
+    return fail(c, CLBM_EINVAL, "bad Nusselt arguments");
+  double h[8];
+  clbm_status st = clbm_reduce_sums(c, 1, which, h);
+  if (st != CLBM_OK) return st;
+  if (!(h[1] > 0)) return fail(c, CLBM_EINVAL, "selection has no wall links");
+  st = finish_sums(c, 1, h, length, dT, nu_out);
+  if (st == CLBM_EUNSTABLE) return fail(c, st, "non-finite wall gradient");
+  return st;
+}
+
 clbm_status clbm_residual(clbm_ctx* c, double* r_out) {
   if (!c || !r_out) return fail(c, CLBM_EINVAL, "bad residual arguments");
-  if (c->t < 1) return fail(c, CLBM_EINVAL, "residual needs one step after initialisation");
-  const long long n = (long long)c->p.nx * c->p.ny;
-  const int nb = red_blocks(n);
-  double* out = c->d_part + kMaxRedBlocks * 8;
-  CLBM_CUDA(c, c->L->residual(make_geom(c), make_coef(c), c->buf[c->cur], c->buf[c->cur ^ 1],
-                              c->d_part, nb, c->stream));
-  CLBM_CUDA(c, launch_reduce_partials(c->d_part, nb, 8, out, c->stream));
   double h[8];
-  CLBM_CUDA(c, cudaMemcpyAsync(h, out, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
-  CLBM_CUDA(c, cudaStreamSynchronize(c->stream));
-  if (h[6] != 0.0 || !std::isfinite(h[0] + h[1] + h[2] + h[3] + h[4] + h[5])) {
-    *r_out = INFINITY;
-    return fail(c, CLBM_EUNSTABLE, "non-finite field values");
-  }
-  double best = 0.0;
-  for (int k = 0; k < 3; ++k) {
-    const double v = std::sqrt(h[2 * k]) / std::max(std::sqrt(h[2 * k + 1]), 1e-30);
-    best = std::max(best, v);
-  }
-  *r_out = best;
-  return CLBM_OK;
+  clbm_status st = clbm_reduce_sums(c, 0, 0, h);
+  if (st != CLBM_OK) return st;
+  st = finish_sums(c, 0, h, 0.0, 1.0, r_out);
+  if (st == CLBM_EUNSTABLE) return fail(c, st, "non-finite field values");
+  return st;
 }
 
 clbm_status clbm_totals(clbm_ctx* c, double* out) {
   if (!c || !out) return fail(c, CLBM_EINVAL, "bad totals arguments");
-  const long long n = (long long)c->p.nx * c->p.ny;
-  const int nb = red_blocks(n);
-  double* red = c->d_part + kMaxRedBlocks * 8;
-  CLBM_CUDA(c, c->L->totals(make_geom(c), c->buf[c->cur], c->d_part, nb, c->stream));
-  CLBM_CUDA(c, launch_reduce_partials(c->d_part, nb, 8, red, c->stream));
   double h[8];
-  CLBM_CUDA(c, cudaMemcpyAsync(h, red, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
-  CLBM_CUDA(c, cudaStreamSynchronize(c->stream));
-  // the stored values are deviations from the rest state: f_i = w_i rho0 + d_i,
-  // g_j = w_j T0 + h_j (the rest state carries no momentum)
-  out[0] = h[4] * c->p.rho0 + h[0];
-  out[1] = h[1];
-  out[2] = h[2];
-  out[3] = h[4] * c->p.T0 + h[3];
-  if (h[5] != 0.0 || !std::isfinite(out[0] + out[1] + out[2] + out[3]))
-    return fail(c, CLBM_EUNSTABLE, "non-finite field values");
-  return CLBM_OK;
+  clbm_status st = clbm_reduce_sums(c, 2, 0, h);
+  if (st != CLBM_OK) return st;
+  st = finish_sums(c, 2, h, 0.0, 1.0, out);
+  if (st == CLBM_EUNSTABLE) return fail(c, st, "non-finite field values");
+  return st;
 }
 
 }  // extern "C"

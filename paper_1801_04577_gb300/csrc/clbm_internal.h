@@ -24,7 +24,13 @@ inline int planes_of(int vh) { return vh ? 15 : 14; }
 // structure-of-arrays: plane q (f_0..f_8, then g_0..g_4) holds ny rows of
 // `pitch` elements, pitch = nx rounded up to a whole warp of vectors.
 struct DevGeom {
-  int nx, ny, pitch, px, py;
+  int nx, ny, pitch, px, py;   // ny: stored rows (own rows plus any ghost rows)
+  // Rows [ylo, yhi) of the storage are updated by the step; the rest are ghost
+  // rows (a y-slab of a larger lattice keeps one on each side, holding its
+  // neighbours' edge rows).  ywlo / ywhi: a box wall lies below row ylo /
+  // above row yhi - 1.  yoff: global row of storage row 0 (stochastic-rounding
+  // keys).  A whole lattice has ylo = 0, yhi = ny, ywlo = ywhi = !py, yoff = 0.
+  int ylo, yhi, ywlo, ywhi, yoff;
   long long plane;             // elements per plane = ny * pitch
   const uint16_t* flags;       // [ny][pitch] or nullptr (box walls only)
   const int32_t* slot;         // [ny][pitch] link slot, -1 = none (masked lattices)

@@ -36,6 +36,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <type_traits>
 
 #include "clbm_internal.h"
@@ -512,8 +513,10 @@ __device__ __forceinline__ void fixup(const DevGeom& g, const Co<R>& c, const S*
     const int ex = ex_of(j), ey = ey_of(j);
     int sx = x - ex, sy = y - ey;
     const bool outx = sx < 0 || sx >= g.nx;
-    const bool outy = sy < 0 || sy >= g.ny;
-    const bool boxwall = (outx && !g.px) || (outy && !g.py);
+    const bool ylow = sy < g.ylo, yhigh = sy >= g.yhi;
+    // beyond the own rows: a box wall, the periodic seam, or a ghost row (read as is)
+    const bool outy = (ylow || yhigh) && g.py;
+    const bool boxwall = (outx && !g.px) || (ylow && g.ywlo) || (yhigh && g.ywhi);
     bool wall = boxwall;
     if (MASK) wall = wall || ((fl >> (j - 1)) & 1u);
     if (wall) {
@@ -534,11 +537,11 @@ __device__ __forceinline__ void fixup(const DevGeom& g, const Co<R>& c, const S*
         else
           have2 = false;
       }
-      if (y2 < 0 || y2 >= g.ny) {
+      if (y2 < g.ylo || y2 >= g.yhi) {
         if (g.py)
           y2 = y2 < 0 ? y2 + g.ny : y2 - g.ny;
-        else
-          have2 = false;
+        else if (y2 < g.ylo ? g.ywlo : g.ywhi)
+          have2 = false;  // beyond a box wall (else: a ghost row)
       }
       const long long i2 = (long long)y2 * g.pitch + x2;
       if (MASK && have2) have2 = (g.flags[i2] & kFlagSolid) == 0;
@@ -590,11 +593,11 @@ __device__ __forceinline__ void fixup(const DevGeom& g, const Co<R>& c, const S*
               else
                 have3 = false;
             }
-            if (y3 < 0 || y3 >= g.ny) {
+            if (y3 < g.ylo || y3 >= g.yhi) {
               if (g.py)
                 y3 = y3 < 0 ? y3 + g.ny : y3 - g.ny;
-              else
-                have3 = false;
+              else if ((y3 < g.ylo ? g.ywlo : g.ywhi) || y3 < 0 || y3 >= g.ny)
+                have3 = false;  // beyond a box wall (slabs reject links whose third node is not stored)
             }
             const long long i3 = (long long)y3 * g.pitch + x3;
             if (MASK && have3) have3 = (g.flags[i3] & kFlagSolid) == 0;
@@ -734,7 +737,7 @@ __device__ __forceinline__ void step_tile(const DevGeom& g, const Co<typename Tr
           if ((skip >> k) & 1u) continue;
           const int x = x0 + k;
           if constexpr (VH) out[14 * plane + k] = from_r<S, R>(qv[k]);
-          const uint32_t key = sr_key(seed, (long long)y * g.pitch + (x & ~3));
+          const uint32_t key = sr_key(seed, (long long)(y + g.yoff) * g.pitch + (x & ~3));
 #pragma unroll
           for (int q = 0; q < 14; ++q) st1<S, R>(out + q * plane + k, v[q][k], stochastic, key, q, x & 3);
         }
@@ -760,7 +763,7 @@ __device__ __forceinline__ void step_tile(const DevGeom& g, const Co<typename Tr
       for (int k = 0; k < V; ++k) {
         const int x = x0 + k;
         if (x == 0 || x == g.nx - 1) continue;
-        const uint32_t key = sr_key(seed, (long long)y * g.pitch + (x & ~3));
+        const uint32_t key = sr_key(seed, (long long)(y + g.yoff) * g.pitch + (x & ~3));
 #pragma unroll
         for (int q = 0; q < 14; ++q) st1<S, R>(out + q * plane + k, v[q][k], stochastic, key, q, x & 3);
       }
@@ -770,7 +773,7 @@ __device__ __forceinline__ void step_tile(const DevGeom& g, const Co<typename Tr
   if constexpr (sizeof(S) == 2) {
     if (stochastic) {
       // x0 is a multiple of V (tiles start at multiples of 32 V nodes)
-      const uint32_t key = sr_key(seed, (long long)y * g.pitch + (x0 & ~3));
+      const uint32_t key = sr_key(seed, (long long)(y + g.yoff) * g.pitch + (x0 & ~3));
 #pragma unroll
       for (int q = 0; q < 14; ++q) {
         uint32_t r0, r1;
@@ -812,7 +815,8 @@ __device__ __forceinline__ void step_node(const DevGeom& g, const Co<typename Tr
   const bool vh = c.vhc != R(0);
   collide_any(c, vh, d, h, qv);
   if (vh) dst[14 * plane + i] = from_r<S, R>(qv);
-  const uint32_t key = sr_key(seed, i - (x & 3));  // the pitch is a multiple of 4
+  // global node index of the group of four (the pitch is a multiple of 4)
+  const uint32_t key = sr_key(seed, i + (long long)g.yoff * g.pitch - (x & 3));
 #pragma unroll
   for (int q = 0; q < 14; ++q) st1<S, R>(dst + q * plane + i, q < 9 ? d[q] : h[q - 9], stochastic, key, q, x & 3);
 }
@@ -835,7 +839,7 @@ __global__ void __launch_bounds__(kStepThreads) step_kernel(const StepArgs a) {
   const int warp = blockIdx.x * (kStepThreads / 32) + (threadIdx.x >> 5);
   const int xw = warp * 32 * V;
   if (xw >= a.g.nx) return;  // whole warps only: the shuffles need all 32 lanes
-  const int y = a.reverse ? a.g.ny - 1 - (int)blockIdx.y : (int)blockIdx.y;
+  const int y = a.g.ylo + (a.reverse ? (int)gridDim.y - 1 - (int)blockIdx.y : (int)blockIdx.y);
   // a tile of solid nodes only: nothing reads them, so neither load nor store
   if (a.g.tile_fluid && !a.g.tile_fluid[(long long)y * a.g.tiles_per_row + warp]) return;
   const Co<R> c = make_co<R>(a.c);
@@ -863,7 +867,7 @@ __global__ void __launch_bounds__(kRedThreads) boundary_kernel(const StepArgs a)
 // interior work instead of following it.
 template <typename S, bool VH, bool MASKED = false>
 __global__ void __launch_bounds__(kStepThreads, 5) step_fused_kernel(const StepArgs a, int nbb,
-                                                                  int xblocks, int y0) {
+                                                                  int xblocks, int y0, int rows) {
   using R = typename Traits<S>::R;
   constexpr int V = Traits<S>::V;
   const Co<R> c = make_co<R>(a.c);
@@ -875,7 +879,6 @@ __global__ void __launch_bounds__(kStepThreads, 5) step_fused_kernel(const StepA
     return;
   }
   const int b = blockIdx.x - nbb;
-  const int rows = a.g.py ? a.g.ny : a.g.ny - 2;
   const int row = b / xblocks;
   const int y = y0 + (a.reverse ? rows - 1 - row : row);
   const int lane = threadIdx.x & 31;
@@ -910,10 +913,10 @@ __global__ void init_kernel(const DevGeom g, const DevCoef cf, S* __restrict__ d
        i += (long long)gridDim.x * blockDim.x) {
     const int y = (int)(i / g.pitch), x = (int)(i - (long long)y * g.pitch);
     R d[9], h[5];
-    bool active = x < g.nx;
+    bool active = x < g.nx && y >= g.ylo && y < g.yhi;  // own rows (ghost rows: zero until exchanged)
     if (g.flags) active = active && !(g.flags[i] & kFlagSolid);
     if (active) {
-      const long long k = (long long)y * g.nx + x;
+      const long long k = (long long)(y - g.ylo) * g.nx + x;
       const R r = rho ? (R)rho[k] : c.rho0;
       const R u = ux ? (R)ux[k] : R(0);
       const R w = uy ? (R)uy[k] : R(0);
@@ -988,11 +991,11 @@ template <typename S>
 __global__ void moments_kernel(const DevGeom g, const DevCoef c, const S* __restrict__ b,
                                double* __restrict__ rho, double* __restrict__ ux,
                                double* __restrict__ uy, double* __restrict__ T) {
-  const long long n = (long long)g.ny * g.nx;
+  const long long n = (long long)(g.yhi - g.ylo) * g.nx;  // own rows
   for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
        k += (long long)gridDim.x * blockDim.x) {
-    const int y = (int)(k / g.nx), x = (int)(k - (long long)y * g.nx);
-    const long long i = (long long)y * g.pitch + x;
+    const int yl = (int)(k / g.nx), x = (int)(k - (long long)yl * g.nx);
+    const long long i = (long long)(yl + g.ylo) * g.pitch + x;
     double r = 0, u = 0, v = 0, t = 0;
     if (!g.flags || !(g.flags[i] & kFlagSolid)) node_macros(c, b, g.plane, i, r, u, v, t);
     if (rho) rho[k] = r;
@@ -1035,11 +1038,11 @@ __global__ void __launch_bounds__(kRedThreads)
     residual_kernel(const DevGeom g, const DevCoef c, const S* __restrict__ cur,
                     const S* __restrict__ prev, double* __restrict__ partials) {
   double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-  const long long n = (long long)g.ny * g.nx;
+  const long long n = (long long)(g.yhi - g.ylo) * g.nx;  // own rows
   for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
        k += (long long)gridDim.x * blockDim.x) {
-    const int y = (int)(k / g.nx), x = (int)(k - (long long)y * g.nx);
-    const long long i = (long long)y * g.pitch + x;
+    const int yl = (int)(k / g.nx), x = (int)(k - (long long)yl * g.nx);
+    const long long i = (long long)(yl + g.ylo) * g.pitch + x;
     if (g.flags && (g.flags[i] & kFlagSolid)) continue;
     double r1, u1, v1, t1, r0, u0, v0, t0;
     node_macros(c, cur, g.plane, i, r1, u1, v1, t1);
@@ -1062,11 +1065,11 @@ template <typename S>
 __global__ void __launch_bounds__(kRedThreads)
     totals_kernel(const DevGeom g, const S* __restrict__ b, double* __restrict__ partials) {
   double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-  const long long n = (long long)g.ny * g.nx;
+  const long long n = (long long)(g.yhi - g.ylo) * g.nx;  // own rows
   for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
        k += (long long)gridDim.x * blockDim.x) {
-    const int y = (int)(k / g.nx), x = (int)(k - (long long)y * g.nx);
-    const long long i = (long long)y * g.pitch + x;
+    const int yl = (int)(k / g.nx), x = (int)(k - (long long)yl * g.nx);
+    const long long i = (long long)(yl + g.ylo) * g.pitch + x;
     if (g.flags && (g.flags[i] & kFlagSolid)) continue;
     double f[9], s = 0.0;
 #pragma unroll
@@ -1299,27 +1302,29 @@ struct LaunchImpl {
     // rest (box lattices; masked ones with their tile classes, whose interior
     // tiles leave the listed nodes out)
     if (!a.g.flags || a.g.tile_fluid) {
-      const int y0 = a.g.py ? 0 : 1;
-      const int rows = a.g.py ? a.g.ny : (a.g.ny > 2 ? a.g.ny - 2 : 0);
+      // interior tiles: the own rows that are not next to a box wall (those are
+      // boundary rows, in the node list)
+      const int y0 = a.g.ylo + a.g.ywlo;
+      const int rows = std::max(0, a.g.yhi - a.g.ywhi - y0);
       const int nbb = (a.nb + kStepThreads - 1) / kStepThreads;
       const long long blocks = (long long)nbb + (long long)xblocks * rows;
       if (blocks > 0 && blocks < (1LL << 31)) {
         const unsigned nblk = (unsigned)blocks;
         if (a.g.flags) {
           if (a.c.vh)
-            step_fused_kernel<S, true, true><<<nblk, kStepThreads, 0, s>>>(a, nbb, xblocks, y0);
+            step_fused_kernel<S, true, true><<<nblk, kStepThreads, 0, s>>>(a, nbb, xblocks, y0, rows);
           else
-            step_fused_kernel<S, false, true><<<nblk, kStepThreads, 0, s>>>(a, nbb, xblocks, y0);
+            step_fused_kernel<S, false, true><<<nblk, kStepThreads, 0, s>>>(a, nbb, xblocks, y0, rows);
         } else {
           if (a.c.vh)
-            step_fused_kernel<S, true><<<nblk, kStepThreads, 0, s>>>(a, nbb, xblocks, y0);
+            step_fused_kernel<S, true><<<nblk, kStepThreads, 0, s>>>(a, nbb, xblocks, y0, rows);
           else
-            step_fused_kernel<S, false><<<nblk, kStepThreads, 0, s>>>(a, nbb, xblocks, y0);
+            step_fused_kernel<S, false><<<nblk, kStepThreads, 0, s>>>(a, nbb, xblocks, y0, rows);
         }
         return cudaGetLastError();
       }
     }
-    dim3 grid(xblocks, a.g.ny);
+    dim3 grid(xblocks, a.g.yhi - a.g.ylo);
     if (a.c.vh)
       step_kernel<S, true><<<grid, kStepThreads, 0, s>>>(a);
     else
@@ -1350,7 +1355,7 @@ struct LaunchImpl {
 
   static cudaError_t moments(const DevGeom& g, const DevCoef& c, const void* buf, double* rho,
                              double* ux, double* uy, double* T, cudaStream_t s) {
-    const long long n = (long long)g.ny * g.nx;
+    const long long n = (long long)(g.yhi - g.ylo) * g.nx;
     moments_kernel<S><<<blocks_for(n, 256), 256, 0, s>>>(g, c, static_cast<const S*>(buf), rho,
                                                           ux, uy, T);
     return cudaGetLastError();
