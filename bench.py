@@ -10,8 +10,11 @@ fluid-node updates per second), whole job.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
 
-Under torchrun with N > 1 every rank advances its own copy of the lattice
-(independent replicas, weak scaling); only the timing is combined (max).
+Under torchrun with N > 1 the Rayleigh-Benard cell has N times the rows and
+is split into y-slabs, one 4096 x 2048 slab per rank, whose edge rows are
+exchanged with the neighbouring ranks after every step (NCCL point-to-point;
+weak scaling); the timing is combined (max over ranks).  --slabs k splits the
+one-GPU lattice into k slabs on that GPU (decomposition overhead).
 The reference arm (--impl reference) times the FP64 CPU oracle on the host
 cores on a bounded sample lattice of the same workload.
 """
@@ -66,9 +69,13 @@ def measured_peak():
         return HBM_FALLBACK_GBS, "fallback"
 
 
-def workload(name: str):
+def workload(name: str, ranks: int = 1):
+    """The named workload; with ranks > 1 the Rayleigh-Benard cell has ranks
+    times the rows (one 4096 x 2048 slab per rank)."""
     if name == "rb4096":
-        return I.rayleigh_benard(4096, 2048)
+        return I.rayleigh_benard(4096, 2048 * ranks)
+    if ranks > 1:
+        raise SystemExit(f"bench.py: workload {name} runs on one GPU only")
     if name == "rb256":
         return I.rayleigh_benard(256, 128)
     if name == "rb2048":
@@ -300,19 +307,33 @@ def run_native(args):
         if world > 1:
             dist.barrier()
 
-    w = workload(args.workload)
+    from paper_1801_04577_gb300 import slabs
+
+    # With N > 1 ranks the lattice is split into y-slabs, one per rank (weak
+    # scaling: the whole lattice has N times the rows of the one-GPU workload);
+    # --slabs k > 1 splits the one-GPU lattice into k slabs on this GPU.
+    mode = "dist" if world > 1 else ("group" if args.slabs > 1 else "single")
+    w = workload(args.workload, world if mode == "dist" else 1)
     p = w.params
-    nodes = I.fluid_count(w)
+    nodes = I.fluid_count(w) // (world if mode == "dist" else 1)  # per rank
     # a dedicated stream: the library launches on it and the events below are
     # recorded on it (torch's default stream has handle 0, which the library
     # would replace by a private stream)
     stream = torch.cuda.Stream(dev)
     torch.cuda.set_stream(stream)
-    s = clbm.from_workload(w, args.precision, stream=stream.cuda_stream, rounding=args.rounding)
+    if mode == "dist":
+        d = slabs.DistSlab(w, args.precision, args.rounding, stream=stream.cuda_stream)
+        run_steps, residual = d.step, d.residual
+    elif mode == "group":
+        g = slabs.SlabGroup(w, args.slabs, args.precision, args.rounding, stream=stream.cuda_stream)
+        run_steps, residual = g.step, g.residual
+    else:
+        s = clbm.from_workload(w, args.precision, stream=stream.cuda_stream, rounding=args.rounding)
+        run_steps, residual = (lambda n: clbm.clbm_step(s.ctx, n)), s.residual
     # clocks are sampled from before the warm-up to the end of the timed region
     sampler = ClockSampler(device_index(local))
     sampler.start()
-    s.step(args.warmup)
+    run_steps(args.warmup)
     torch.cuda.synchronize()
     barrier()
     torch.cuda.synchronize()
@@ -320,20 +341,47 @@ def run_native(args):
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    clbm.clbm_step(s.ctx, args.steps)
+    run_steps(args.steps)
     e1.record(stream)
     torch.cuda.synchronize()
     clocks = sampler.stop()
     barrier()
     el_ms = e0.elapsed_time(e1)
     # the state must still be finite after the timed steps
-    res = s.residual()
+    res = residual()
 
     el_ms, value = combine_ranks(el_ms, nodes, args.steps, dev)
 
     # end to end through the public API: host fields in, solve, host fields out
     e2e = None
-    if not args.no_e2e:
+    if not args.no_e2e and mode != "single":
+        rows = d.rows if mode == "dist" else p.ny
+        n = p.nx * rows
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        if mode == "dist":
+            d.slab.init(I.Fields(T=w.init.T))
+            d.exchange()
+            d.step(args.steps)
+            out = d.slab.moments()
+        else:
+            for sl in g.slabs:
+                sl.init(I.Fields(T=w.init.T))
+            g.exchange()
+            g.step(args.steps)
+            out = g.moments()
+        el2 = time.perf_counter() - t0
+        el2_t = torch.tensor([el2], dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.all_reduce(el2_t, op=dist.ReduceOp.MAX)
+        el2 = float(el2_t.item())
+        e2e = {"value": world * nodes * args.steps / el2 / 1e6, "unit": "MLUPS",
+               "h2d_bytes_per_step": 8 * n / args.steps, "d2h_bytes_per_step": 4 * 8 * n / args.steps,
+               "note": f"per rank: slab initialisation from host T ({8 * n} B), halo exchange, "
+                       f"{args.steps} steps with halo exchanges, moments (rho, ux, uy, T) to host "
+                       f"({32 * n} B); bytes reported per lattice step"}
+    if not args.no_e2e and mode == "single":
         n = p.nx * p.ny
         T_host = torch.from_numpy(w.init.T.astype("float64").ravel()).pin_memory()
         outs = [torch.empty(n, dtype=torch.float64).pin_memory() for _ in range(3)]
@@ -369,13 +417,16 @@ def run_native(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": DTYPE[args.precision], "data": "synthetic",
             "config": dict(workload_config(w, args.workload, args.precision),
-                           parallelism=f"replicas{world}" if world > 1 else "single"),
+                           parallelism={"dist": f"yslab{world} (one slab per GPU, NCCL halo exchange)",
+                                        "group": f"yslab{args.slabs} on one GPU (device halo copies)",
+                                        "single": "single"}[mode]),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "kernel": step_kernel_name(w),
                          "peak_kind": peak_kind,
                          "algorithmic_bytes_per_launch": bytes_lu * nodes},
-            "gpu_launches": step_launches(w, args.steps),
+            "gpu_launches": step_launches(w, args.steps) if mode == "single" else args.steps * (
+                args.slabs if mode == "group" else 1),
             "residual_after": res}
     if e2e is not None:
         line["e2e"] = e2e
@@ -385,7 +436,7 @@ def run_native(args):
         line["cpu_baseline"] = time_oracle()
     if rank == 0:
         print(json.dumps(line), flush=True)
-    s.close()
+    {"dist": lambda: d.close(), "group": lambda: g.close(), "single": lambda: s.close()}[mode]()
     if world > 1:
         dist.destroy_process_group()
     return 0
@@ -555,6 +606,8 @@ def main():
                     help="16-bit storage: 0 = nearest even, 1 = stochastic")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--slabs", type=int, default=1,
+                    help="one GPU: split the lattice into this many y-slabs (halo copies each step)")
     ap.add_argument("--batch-size", type=int, default=512)
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--check-every", type=int, default=100)

@@ -60,8 +60,14 @@ def test_slabs_reproduce_the_single_lattice_bit_for_bit(name, precision, roundin
             side_periodic = w.params.periodic_x if which < 2 else w.params.periodic_y
             if side_periodic:
                 continue
-            assert g.nusselt(which, w.length, w.dT) == pytest.approx(
-                ref.nusselt(which, w.length, w.dT), rel=1e-12, abs=1e-14)
+            try:
+                nu_ref = ref.nusselt(which, w.length, w.dT)
+            except clbm.ClbmError as e:  # a side without fluid nodes (the annulus box)
+                assert e.status == clbm.CLBM_EINVAL
+                with pytest.raises(clbm.ClbmError):
+                    g.nusselt(which, w.length, w.dT)
+                continue
+            assert g.nusselt(which, w.length, w.dT) == pytest.approx(nu_ref, rel=1e-12, abs=1e-14)
         g.close()
     ref.close()
 
