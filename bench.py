@@ -452,7 +452,7 @@ def run_batch(args):
     dev = torch.device("cuda", 0)
     stream = torch.cuda.Stream(dev)
     torch.cuda.set_stream(stream)
-    ws = I.random_cavities(args.batch_size)
+    ws = I.random_cavities(args.batch_size, hmax=args.batch_hmax)
     nodes = np.array([w.params.nx * w.params.ny for w in ws], dtype=np.int64)
     t0 = time.perf_counter()
     b = clbm.Batch(ws, args.precision, rounding=args.rounding, autotune=True, stream=stream.cuda_stream)
@@ -483,16 +483,21 @@ def run_batch(args):
             "steps": int(steps), "warmup": int(warm_steps), "ms_per_step": el / max(steps, 1) * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": DTYPE[args.precision], "data": "synthetic",
-            "config": {"workload": f"batch_{len(ws)}_random_cavities_{args.precision}",
+            "config": {"workload": f"batch_{len(ws)}_random_cavities_h32-{args.batch_hmax}_{args.precision}"
+                                   + ("_sr" if args.rounding else ""),
                        "total_nodes": int(nodes.sum()), "tol": args.tol, "step_cap": args.steps,
                        "check_every": args.check_every, "rounding": args.rounding},
             "roofline": {"bound": "hbm", "achieved": bytes_lu * updates / el / 1e9, "peak": peak,
                          "unit": "GB/s", "frac": bytes_lu * updates / el / 1e9 / peak,
                          "traffic": None, "kernel": "clbm::batch_step_kernel (whole solve)",
                          "peak_kind": peak_kind},
-            "batch": {"converged": int((conv > 0).sum()), "diverged": int((conv == -2).sum()),
+            "batch": {"converged": int((conv > 0).sum()), "converged_fraction": float((conv > 0).mean()),
+                      "diverged": int((conv == -2).sum()),
+                      "time_to_solution_s": el if (conv > 0).all() else None,
                       "not_converged": int((conv == -1).sum()),
                       "median_steps_converged": float(np.median(conv[conv > 0])) if (conv > 0).any() else None,
+                      "residual_quantiles_10_50_90": [float(v) for v in np.quantile(
+                          res[np.isfinite(res)], [0.1, 0.5, 0.9])] if np.isfinite(res).any() else None,
                       "create_s": t_create, "solve_s": el,
                       "tile_widths": {str(k): widths.count(k) for k in (32, 64, 128)}},
             "gpu_launches": launches}
@@ -609,6 +614,8 @@ def main():
     ap.add_argument("--slabs", type=int, default=1,
                     help="one GPU: split the lattice into this many y-slabs (halo copies each step)")
     ap.add_argument("--batch-size", type=int, default=512)
+    ap.add_argument("--batch-hmax", type=int, default=512,
+                    help="batch512: largest cavity side (sides drawn from 32..hmax)")
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--check-every", type=int, default=100)
     ap.add_argument("--net-batch", type=int, default=32)

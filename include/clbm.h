@@ -147,6 +147,18 @@ clbm_status clbm_set_boundaries(clbm_ctx* ctx, const uint8_t* solid, const clbm_
                                 int32_t n_tbc, const int32_t* side_tbc, const clbm_link* links,
                                 int32_t n_links);
 
+/* Velocity (ux, uy) of box side `side` (0 = x0, 1 = x1, 2 = y0, 3 = y1), for
+ * flows driven by a moving wall such as thermal Couette flow.  Not part of the
+ * paper, whose walls are at rest: a population f_i* reflected at a moving side
+ * returns as f_ibar = f_i* - 2 w_i rho0 (e_i . u_w) / cs^2 (the bounce-back of
+ * Ladd, J. Fluid Mech. 271, 1994; e_i toward the wall, cs^2 = 1/3).  The
+ * temperature rule (Eq. 26-28) is unchanged: for a wall moving along itself
+ * the D2Q5 populations crossing it carry no velocity term.  A diagonal link
+ * into a box corner takes the velocity of the x side when x is not periodic.
+ * Periodic sides ignore their velocity.  All sides start at rest.
+ * Errors: CLBM_EINVAL for side outside 0..3 or a non-finite velocity. */
+clbm_status clbm_set_wall_velocity(clbm_ctx* ctx, int32_t side, double ux, double uy);
+
 /* Set the state to the equilibrium distributions whose central moments are
  * Eq. 9 and Eq. 19 at the given fields, i.e. f(t=0) = f^eq(rho, u),
  * g(t=0) = g^eq(T, u), and reset the step counter.  Each pointer is an FP64

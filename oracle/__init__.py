@@ -89,6 +89,8 @@ def lib():
         L.oref_equilibrium.argtypes = [vp, C.c_double, C.c_double, C.c_double, C.c_double, dp, dp]
         L.oref_rates.argtypes = [vp, dp]
         L.oref_inverse_matrices.argtypes = [vp, dp, dp]
+        L.oref_set_wall_velocity.argtypes = [vp, C.c_int32, C.c_double, C.c_double]
+        L.oref_set_wall_velocity.restype = C.c_int
         L.oref_threads.restype = C.c_int
         L.oref_set_threads.argtypes = [C.c_int]
         _lib = L
@@ -147,6 +149,9 @@ class Oracle:
         if st != 0:
             raise ValueError(f"oracle rejected the problem description (status {st})")
         self._h = h
+        for side, (ux, uy) in enumerate(getattr(geom, "side_u", None) or ()):
+            if ux or uy:
+                self.set_wall_velocity(side, ux, uy)
         self.init(init)
 
     def __del__(self):
@@ -197,6 +202,11 @@ class Oracle:
         if lib().oref_residual(self._h, C.byref(out)) != 0:
             raise ValueError("residual needs at least one step")
         return out.value
+
+    def set_wall_velocity(self, side: int, ux: float, uy: float = 0.0):
+        """Velocity of a box side for the moving-wall bounce-back (not in the paper)."""
+        if lib().oref_set_wall_velocity(self._h, int(side), float(ux), float(uy)) != 0:
+            raise ValueError("bad side")
 
     def collide_node(self, f, g):
         f = _f64(f)

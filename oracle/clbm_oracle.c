@@ -58,6 +58,10 @@
 /* ---------------- lattice (Eq. 3) ---------------- */
 static const int EX[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
 static const int EY[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+/* D2Q9 rest weights (the Eq. 9 equilibrium at rho = 1, u = 0); used only by
+ * the moving-wall bounce-back, which is not part of the paper */
+static const double W9[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9,
+                             1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
 
 static int opposite(int i) {
   for (int j = 0; j < 9; ++j)
@@ -190,6 +194,7 @@ typedef struct {
   double *f, *g, *fn, *gn;     /* pre-collision DFs at t, and at t+1        */
   double *T, *rho, *ux, *uy;   /* macroscopic fields at time t (of the last step) */
   double* Qn;                  /* total heat source per node at time t          */
+  double uw[4][2];             /* velocity of each box side (x0, x1, y0, y1); 0 = at rest */
   int have_prev;
   int64_t steps;
 } oref_ctx;
@@ -642,6 +647,13 @@ static void step_once(oref_ctx* c) {
         if (q == 0.5 || (q < 0.5 && !have_b)) {
           /* half-way bounce-back: the DF returns to x_f reversed */
           c->fn[9 * k + opp[i]] = fs[i];
+          if (side >= 0) {
+            /* a moving box side (not in the paper; the bounce-back of Ladd,
+             * J. Fluid Mech. 271, 1994): the reflected DF gains
+             * -2 w_i rho0 (e_i . u_w) / cs^2 */
+            const double eu = EX[i] * c->uw[side][0] + EY[i] * c->uw[side][1];
+            c->fn[9 * k + opp[i]] -= 6.0 * W9[i] * c->p.rho0 * eu;
+          }
         } else if (q < 0.5) {
           /* f_i* interpolated to the point 1 - 2q behind x_f, which reaches x_f reflected */
           c->fn[9 * k + opp[i]] = 2.0 * q * fs[i] + (1.0 - 2.0 * q) * c->fs[9 * idx(c, xb, yb) + i];
@@ -860,6 +872,16 @@ int oref_threads(void) {
 #else
   return 1;
 #endif
+}
+
+/* Velocity of box side `side` (0 = x0, 1 = x1, 2 = y0, 3 = y1) for the
+ * moving-wall bounce-back (not in the paper; used for thermal Couette flow). */
+int oref_set_wall_velocity(void* h, int32_t side, double ux, double uy) {
+  oref_ctx* c = (oref_ctx*)h;
+  if (side < 0 || side > 3) return OREF_EINVAL;
+  c->uw[side][0] = ux;
+  c->uw[side][1] = uy;
+  return OREF_OK;
 }
 
 void oref_set_threads(int n) {

@@ -52,7 +52,7 @@ EXPORTS = ["clbm_create", "clbm_set_boundaries", "clbm_init_fields", "clbm_step"
            "clbm_nusselt", "clbm_residual", "clbm_totals", "clbm_residual_fields_noalloc", "clbm_batch_create",
            "clbm_batch_solve", "clbm_batch_lattice", "clbm_batch_tile_width", "clbm_batch_destroy",
            "clbm_damp_period2", "clbm_batch_damp_period2",
-           "clbm_create_slab", "clbm_halo_bytes", "clbm_halo_pack", "clbm_halo_unpack", "clbm_halo_copy",
+           "clbm_set_wall_velocity", "clbm_create_slab", "clbm_halo_bytes", "clbm_halo_pack", "clbm_halo_unpack", "clbm_halo_copy",
            "clbm_slabs_exchange", "clbm_slabs_step", "clbm_reduce_sums", "clbm_finish_sums",
            "clbm_batch_last_error", "clbm_time", "clbm_destroy", "clbm_last_error",
            "clbm_status_string"]
@@ -103,6 +103,7 @@ def load(path: Optional[str] = None):
     L.clbm_batch_destroy.argtypes = [vp]
     L.clbm_damp_period2.argtypes = [vp]
     L.clbm_batch_damp_period2.argtypes = [vp]
+    L.clbm_set_wall_velocity.argtypes = [vp, C.c_int32, C.c_double, C.c_double]
     L.clbm_create_slab.argtypes = [C.POINTER(clbm_params), C.c_int32, C.c_int32, vp, C.POINTER(vp)]
     L.clbm_halo_bytes.argtypes = [vp, C.POINTER(C.c_int64)]
     L.clbm_halo_pack.argtypes = [vp, C.c_int32, vp]
@@ -231,6 +232,16 @@ def clbm_residual_fields_noalloc(T_now, ux_now, uy_now, T_prev, ux_prev, uy_prev
     return out.value
 
 
+def clbm_set_wall_velocity(ctx, side: int, ux: float, uy: float = 0.0):
+    _check(load().clbm_set_wall_velocity(ctx, int(side), float(ux), float(uy)), ctx, "clbm_set_wall_velocity")
+
+
+def _apply_side_velocities(ctx, geom):
+    for side, (ux, uy) in enumerate(getattr(geom, "side_u", None) or ()):
+        if ux or uy:
+            clbm_set_wall_velocity(ctx, side, ux, uy)
+
+
 def clbm_create_slab(params: clbm_params, y0: int, rows: int, stream: Optional[int] = None) -> C.c_void_p:
     L = load()
     ctx = C.c_void_p()
@@ -324,6 +335,7 @@ class Solver:
         if geom is not None:
             clbm_set_boundaries(self.ctx, geom.solid, geom.tbc, geom.side_tbc, geom.link_node,
                                 geom.link_dir, geom.link_ne, geom.link_tbc, geom.link_q_or_half())
+            _apply_side_velocities(self.ctx, geom)
         if init is not None:
             self.init(init)
 
@@ -386,6 +398,7 @@ class Slab(Solver):
         if geom is not None:
             clbm_set_boundaries(self.ctx, geom.solid, geom.tbc, geom.side_tbc, geom.link_node,
                                 geom.link_dir, geom.link_ne, geom.link_tbc, geom.link_q_or_half())
+            _apply_side_velocities(self.ctx, geom)
         if init is not None:
             self.init(init)
 
@@ -466,6 +479,8 @@ class Batch:
         items = []
         for w in self.workloads:
             p, g = w.params, w.geom
+            if any(ux or uy for ux, uy in (getattr(g, "side_u", None) or ())):
+                raise ValueError(f"{w.name}: batched lattices have walls at rest")
             shape = (p.ny, p.nx)
             tbc = (clbm_tbc * max(len(g.tbc), 1))(*[clbm_tbc(*map(float, t)) for t in g.tbc])
             nl = g.n_links

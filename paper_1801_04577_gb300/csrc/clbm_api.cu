@@ -70,6 +70,7 @@ struct clbm_ctx {
   std::vector<clbm_link> h_links;  // links of own-row nodes, node = stored row * nx + x
   int side_tbc[4] = {-1, -1, -1, -1};
   double side_b[4][3] = {};
+  double side_u[4][2] = {};  // moving box sides (clbm_set_wall_velocity)
   // scratch
   double* d_fields = nullptr;  // 4 * nx * ny doubles, allocated on first use
   double* d_part = nullptr;    // reduction partials + result
@@ -141,6 +142,14 @@ static DevGeom make_geom(const clbm_ctx* c) {
   std::memcpy(g.side_b, c->side_b, sizeof(g.side_b));
   for (int sd = 0; sd < 4; ++sd)
     for (int k = 0; k < 3; ++k) g.side_bf[sd][k] = (float)c->side_b[sd][k];
+  g.moving = 0;
+  g.pad_moving = 0;
+  for (int sd = 0; sd < 4; ++sd)
+    for (int k = 0; k < 2; ++k) {
+      g.side_u[sd][k] = c->side_u[sd][k];
+      g.side_uf[sd][k] = (float)c->side_u[sd][k];
+      if (c->side_u[sd][k] != 0.0) g.moving = 1;
+    }
   return g;
 }
 
@@ -784,6 +793,16 @@ clbm_status clbm_slabs_step(clbm_ctx* const* slabs, int32_t n, int32_t periodic,
     clbm_status st = clbm_slabs_exchange(slabs, n, periodic);
     if (st != CLBM_OK) return st;
   }
+  return CLBM_OK;
+}
+
+clbm_status clbm_set_wall_velocity(clbm_ctx* c, int32_t side, double ux, double uy) {
+  if (!c || side < 0 || side > 3 || !std::isfinite(ux) || !std::isfinite(uy))
+    return fail(c, CLBM_EINVAL, "bad wall velocity");
+  CLBM_CUDA(c, cudaStreamSynchronize(c->stream));
+  drop_graphs(c);  // captured steps hold the old wall description
+  c->side_u[side][0] = ux;
+  c->side_u[side][1] = uy;
   return CLBM_OK;
 }
 

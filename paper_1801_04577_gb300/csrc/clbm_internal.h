@@ -43,6 +43,11 @@ struct DevGeom {
   int tiles_per_row, pad_tiles;
   double side_b[4][3];         // conditions of the box sides x0, x1, y0, y1
   float side_bf[4][3];         // the same rounded to FP32 (for FP32 arithmetic)
+  // moving box sides (not in the paper): wall velocity of each side, and the
+  // same rounded to FP32; moving = 0 when every side is at rest
+  double side_u[4][2];
+  float side_uf[4][2];
+  int moving, pad_moving;
 };
 
 // Relaxation and forcing constants in FP64 (converted to the compute type

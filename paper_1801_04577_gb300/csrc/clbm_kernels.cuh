@@ -548,6 +548,21 @@ __device__ __forceinline__ void fixup(const DevGeom& g, const Co<R>& c, const S*
       const R fi = to_r(src[i * plane + own]);
       if (q == R(0.5) || (q < R(0.5) && !have2)) {
         d[j] = fi;  // half-way bounce-back
+        if (boxwall && g.moving) {
+          // a moving box side (not in the paper; Ladd's bounce-back): the
+          // reflected population gains -6 w_i rho0 (e_i . u_w), e_i = -e_j
+          const int sd = (outx && !g.px) ? (sx < 0 ? 0 : 1) : (ylow ? 2 : 3);
+          R uwx, uwy;
+          if constexpr (std::is_same<R, float>::value) {
+            uwx = g.side_uf[sd][0];
+            uwy = g.side_uf[sd][1];
+          } else {
+            uwx = (R)g.side_u[sd][0];
+            uwy = (R)g.side_u[sd][1];
+          }
+          const R w6 = j <= 4 ? R(6.0 / 9.0) : R(6.0 / 36.0);
+          d[j] += w6 * c.rho0 * (R(ex) * uwx + R(ey) * uwy);
+        }
       } else if (q < R(0.5)) {  // f_i* interpolated to the point 1 - 2q behind x_f
         d[j] = R(2) * q * fi + (R(1) - R(2) * q) * to_r(src[i * plane + i2]);
       } else {  // the reflected value, 2q - 1 beyond x_f, interpolated with f_j* at x_f

@@ -83,6 +83,9 @@ class Geometry:
     # fraction q in (0, 1] of each link from the fluid node to the wall; None = 1/2 for
     # every link (the paper's half-way walls).  Links of directions 5..8 carry only q.
     link_q: Optional[np.ndarray] = None
+    # velocity (ux, uy) of each box side x0, x1, y0, y1 for the moving-wall
+    # bounce-back (not in the paper); None = every side at rest
+    side_u: Optional[Tuple[Tuple[float, float], ...]] = None
 
     @property
     def n_links(self) -> int:
@@ -435,6 +438,38 @@ def dissipation_channel(L: int = 16, nu: float = 0.1, alpha: float = 0.1, Fx: fl
     g = Geometry(tbc=[dirichlet(Tw)], side_tbc=(-1, -1, 0, 0))
     return Workload(f"dissipation_{L}", p, g, Fields(T=np.full((L, nx), Tw)), length=float(L),
                     u_scale=Fx * L * L / (8.0 * nu))
+
+
+def couette_channel(H: int = 16, Uw: float = 0.05, nu: float = 0.1, alpha: float = 0.1,
+                    T_bottom: float = 1.0, T_top: float = 0.0, nx: int = 4,
+                    viscous_heating: int = 0) -> Workload:
+    """Thermal Couette flow (not in the paper): periodic in x, a wall at rest
+    at y = 0 held at T_bottom and a wall at y = H moving along +x at Uw held at
+    T_top (Dirichlet).  couette_exact gives the steady solution."""
+    s_nu, lambda1 = rates_from_diffusivities(nu, alpha)
+    p = Params(nx=nx, ny=H, periodic_x=1, s_nu=s_nu, s_b=s_nu, lambda1=lambda1,
+               T0=0.5 * (T_bottom + T_top), viscous_heating=viscous_heating)
+    g = Geometry(tbc=[dirichlet(T_bottom), dirichlet(T_top)], side_tbc=(-1, -1, 0, 1),
+                 side_u=((0.0, 0.0), (0.0, 0.0), (0.0, 0.0), (Uw, 0.0)))
+    return Workload(f"couette_{H}{'_vh' if viscous_heating else ''}", p, g,
+                    Fields(T=np.full((H, nx), p.T0)), length=float(H), dT=abs(T_bottom - T_top) or 1.0,
+                    u_scale=Uw)
+
+
+def couette_exact(w: Workload, nu: float, alpha: float, T_bottom: float = 1.0,
+                  T_top: float = 0.0):
+    """(u_x, T) at the node centres s = y + 1/2 of couette_channel: u = Uw s / H;
+    T = T_bottom + (T_top - T_bottom) s / H, plus Q_v s (H - s) / (2 alpha) with
+    the uniform viscous source Q_v = nu (Uw / H)^2 when it is on (alpha T'' = -Q_v)."""
+    H = w.params.ny
+    Uw = w.geom.side_u[3][0]
+    s = np.arange(H, dtype=np.float64) + 0.5
+    u = Uw * s / H
+    T = T_bottom + (T_top - T_bottom) * s / H
+    if w.params.viscous_heating:
+        Qv = nu * (Uw / H) ** 2
+        T = T + Qv * s * (H - s) / (2.0 * alpha)
+    return u, T
 
 
 def dissipation_exact(L: int, nu: float, alpha: float, Fx: float, Tw: float = 0.0) -> np.ndarray:

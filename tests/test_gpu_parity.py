@@ -317,3 +317,33 @@ def test_all_fluid_mask_is_bit_identical_to_the_box(precision, rounding, name):
     b.step(41)
     for x, y in zip(a.moments(), b.moments()):
         np.testing.assert_array_equal(x, y)
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+@pytest.mark.parametrize("vh", [0, 1])
+def test_thermal_couette_matches_oracle(precision, vh):
+    """Thermal Couette flow (moving top wall, not in the paper) against the
+    oracle while the profiles develop (2,000 steps), and, in FP64, the steady
+    profiles against the closed form as the oracle pin states them."""
+    nu, alpha, H, Uw = 0.1, 0.08, 16, 0.05
+    w = I.couette_channel(H, Uw, nu, alpha, viscous_heating=vh)
+    # u_y and rho - rho0 vanish in the exact Couette flow: compared against U and rho0
+    errs, _ = run_pair(w, 2000, precision, vanishing=("rho", "uy"))
+    _assert_within(errs, TOL[precision], f"couette vh={vh} {precision}")
+    if precision == "f64":
+        s = clbm.from_workload(w, "f64")
+        s.step(int(40 * H * H / min(nu, alpha)))
+        _, ux, _, T = s.moments()
+        u_ex, T_ex = I.couette_exact(w, nu, alpha)
+        assert np.abs(ux[:, 0] - u_ex).max() < 1e-12 * Uw
+        lin = 1 - (np.arange(H) + 0.5) / H
+        tol = 1e-5 * (T_ex - lin).max() if vh else 1e-11
+        assert np.abs(T[:, 0] - T_ex).max() < tol
+
+
+def test_moving_wall_velocity_rejects_bad_side():
+    w = I.couette_channel()
+    s = clbm.from_workload(w, "f32")
+    with pytest.raises(clbm.ClbmError) as ei:
+        clbm.clbm_set_wall_velocity(s.ctx, 4, 0.1)
+    assert ei.value.status == clbm.CLBM_EINVAL

@@ -495,3 +495,37 @@ def test_residual_is_the_relative_l2_change_of_T_and_u(name):
     for norm in (lambda v: np.abs(v).sum(), lambda v: np.abs(v).max()):
         alt = max(norm(m1[k][fluid] - m0[k][fluid]) / norm(m1[k][fluid]) for k in (3, 1, 2))
         assert abs(alt - r) > 1e-3 * r
+
+
+# ---------------------------------------------------------------------------
+# Thermal Couette flow (not in the paper: the moving wall uses the standard
+# bounce-back of Ladd, 1994, with rho0)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("vh", [0, 1])
+def test_thermal_couette_exact(vh):
+    """A wall moving at Uw over a wall at rest: the steady velocity is linear
+    and the temperature linear between the Dirichlet walls -- plus, with the
+    viscous source of Sec. 3.2, the parabola of the uniform dissipation
+    nu (Uw/H)^2 -- and the scheme reproduces the velocity and the linear
+    temperature to rounding (half-way walls; such profiles are exact for it,
+    cf. Sec. 3.1).  The source read from the non-equilibrium moments carries,
+    besides nu (du/dy)^2, a normal-stress term of relative size about
+    (3 nu du/dy)^2 = 9e-7 here (second order in the Knudsen number), so the
+    dissipation parabola (amplitude 3.9e-4) is met to 1e-5 of itself.  A wrong
+    sign or weight in the wall's momentum term, or a source that is not
+    nu (du/dy)^2, changes the profiles at O(1)."""
+    nu, alpha, H, Uw = 0.1, 0.08, 16, 0.05
+    w = I.couette_channel(H, Uw, nu, alpha, viscous_heating=vh)
+    o = oracle.from_workload(w)
+    o.step(int(40 * H * H / min(nu, alpha)))
+    _, ux, uy, T = o.moments()
+    u_ex, T_ex = I.couette_exact(w, nu, alpha)
+    assert np.abs(ux[:, 0] - u_ex).max() < 1e-12 * Uw
+    assert np.abs(uy).max() < 1e-14
+    lin = 1 - (np.arange(H) + 0.5) / H
+    if vh:
+        amp = (T_ex - lin).max()  # the dissipation parabola, 3.9e-4
+        assert amp > 1e-4
+        assert np.abs(T[:, 0] - T_ex).max() < 1e-5 * amp
+    else:
+        assert np.abs(T[:, 0] - T_ex).max() < 1e-11
