@@ -312,7 +312,12 @@ __host__ __device__ __forceinline__ void collide(const Co<R>& c, R (&d)[9], R (&
   const R rho = c.rho0 + drho;
   const R jx = (d[1] - d[3]) + (d[5] - d[6]) + (d[8] - d[7]);
   const R jy = (d[2] - d[4]) + (d[5] - d[7]) + (d[6] - d[8]);
-  const R inv_rho = R(1) / rho;
+  // FP32: the reciprocal to within 2 ulp (hardware approximation), which the
+  // FP32 parity bound leaves ample room for; FP64: the exact quotient
+  R inv_rho = R(1) / rho;
+#ifdef __CUDA_ARCH__
+  if constexpr (std::is_same<R, float>::value) inv_rho = __fdividef(1.0f, rho);
+#endif
   const R ux = (jx + R(0.5) * Fx) * inv_rho;
   const R uy = (jy + R(0.5) * Fy) * inv_rho;
 
