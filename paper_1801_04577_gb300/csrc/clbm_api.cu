@@ -719,7 +719,7 @@ clbm_status clbm_halo_bytes(const clbm_ctx* c, int64_t* bytes) {
   return CLBM_OK;
 }
 
-// One row of every plane of the current state: row `row` of buffer `buf`.
+// One row of every plane of the current state.
 static char* row_ptr(const clbm_ctx* c, int row) {
   return static_cast<char*>(c->buf[c->cur]) + (size_t)row * c->pitch * c->L->elem_bytes;
 }
@@ -772,6 +772,30 @@ clbm_status clbm_slabs_exchange(clbm_ctx* const* slabs, int32_t n, int32_t perio
   if (!slabs || n < 1) return CLBM_EINVAL;
   for (int k = 0; k < n; ++k)
     if (!slabs[k] || !slabs[k]->slab) return CLBM_EINVAL;
+  // One stream, one device, one format: every seam in one kernel launch (the
+  // rows are copied whole, pitch included, so the copies are 16-byte words).
+  bool one = 2 * n <= kMaxHaloCopies;
+  for (int k = 1; k < n && one; ++k)
+    one = slabs[k]->stream == slabs[0]->stream && slabs[k]->L == slabs[0]->L &&
+          slabs[k]->pitch == slabs[0]->pitch && plane_count(slabs[k]) == plane_count(slabs[0]);
+  if (one) {
+    HaloTable t{};
+    const size_t eb = slabs[0]->L->elem_bytes;
+    t.planes = plane_count(slabs[0]);
+    t.row_bytes = (long long)slabs[0]->pitch * (long long)eb;
+    for (int k = 0; k < n; ++k) {
+      const int up = k + 1 < n ? k + 1 : (periodic ? 0 : -1);
+      if (up < 0) continue;
+      clbm_ctx *a = slabs[k], *b = slabs[up];
+      // a's last own row -> the ghost row below b; b's first own row -> the ghost row above a
+      t.c[t.n++] = HaloCopy{row_ptr(a, a->yhi - 1), row_ptr(b, b->ylo - 1), a->plane * (long long)eb,
+                            b->plane * (long long)eb};
+      t.c[t.n++] = HaloCopy{row_ptr(b, b->ylo), row_ptr(a, a->yhi), b->plane * (long long)eb,
+                            a->plane * (long long)eb};
+    }
+    CLBM_CUDA(slabs[0], launch_halo(t, slabs[0]->stream));
+    return CLBM_OK;
+  }
   for (int k = 0; k < n; ++k) {
     const int up = k + 1 < n ? k + 1 : (periodic ? 0 : -1);
     if (up < 0) continue;

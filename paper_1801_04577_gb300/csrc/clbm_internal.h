@@ -204,6 +204,21 @@ void set_view_time(clbm_ctx* c, int64_t t, int cur);
 cudaError_t launch_advance(long long* t, int k, cudaStream_t s);
 cudaError_t launch_set_step(long long* t, long long v, cudaStream_t s);
 
+// Halo rows of slabs held by one process: each entry copies one row of every
+// plane (row_bytes, a multiple of 16, at planes plane strides) from src to dst.
+constexpr int kMaxHaloCopies = 32;
+struct HaloCopy {
+  const char* src;
+  char* dst;
+  long long splane, dplane;  // plane strides in bytes
+};
+struct HaloTable {
+  HaloCopy c[kMaxHaloCopies];
+  int n, planes;
+  long long row_bytes;
+};
+cudaError_t launch_halo(const HaloTable& t, cudaStream_t s);
+
 // Fixed-order sum of nblocks x width partials into out[width] (one block).
 cudaError_t launch_reduce_partials(const double* partials, int nblocks, int width, double* out,
                                    cudaStream_t s);

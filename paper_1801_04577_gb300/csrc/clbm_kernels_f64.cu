@@ -34,6 +34,27 @@ cudaError_t launch_advance(long long* t, int k, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// All halo rows of an exchange in one launch: blockIdx.y = copy, 16-byte words.
+__global__ void halo_kernel(const HaloTable t) {
+  const HaloCopy h = t.c[blockIdx.y];
+  const long long words = t.row_bytes / 16;
+  const long long total = words * t.planes;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long q = i / words, w = i - q * words;
+    *reinterpret_cast<uint4*>(h.dst + q * h.dplane + 16 * w) =
+        *reinterpret_cast<const uint4*>(h.src + q * h.splane + 16 * w);
+  }
+}
+
+cudaError_t launch_halo(const HaloTable& t, cudaStream_t s) {
+  if (t.n <= 0) return cudaSuccess;
+  const long long total = t.row_bytes / 16 * t.planes;
+  const int bx = (int)std::min<long long>((total + 255) / 256, 1024);
+  halo_kernel<<<dim3(bx, t.n), 256, 0, s>>>(t);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_reduce_partials(const double* partials, int nblocks, int width, double* out,
                                    cudaStream_t s) {
   reduce_partials_kernel<<<1, kRedThreads, 0, s>>>(partials, nblocks, width, out);
