@@ -433,8 +433,9 @@ def run_native(args):
                          "kernel": step_kernel_name(w),
                          "peak_kind": peak_kind,
                          "algorithmic_bytes_per_launch": bytes_lu * nodes},
+            # slabs: one step launch per slab per step, plus (one process) one halo-copy launch
             "gpu_launches": step_launches(w, args.steps) if mode == "single" else args.steps * (
-                args.slabs if mode == "group" else 1),
+                args.slabs + 1 if mode == "group" else 1),
             "residual_after": res}
     if e2e is not None:
         line["e2e"] = e2e
