@@ -663,141 +663,6 @@ __device__ __forceinline__ void st1(S* p, R v, int stochastic, uint32_t key, int
 // next to solids come out wrong here and are recomputed afterwards by the
 // boundary kernel from its precomputed node list.  Keeping the walls out of
 // this kernel keeps its warps free of divergent wall code.
-// 16-bit storage, four nodes per lane: the interior update of step_tile with
-// the loaded values kept as raw 16-bit pairs in 32-bit words (two words per
-// plane) through the x-shift -- the shift is a warp shuffle of one word and a
-// byte permutation -- and unpacked to FP32 two nodes at a time for the
-// collision, whose results are packed back into the same words.  This keeps
-// half the live state of the FP32 form (no spills at five blocks per SM).
-template <typename S>
-__device__ __forceinline__ float2 unpack2(uint32_t w);
-template <>
-__device__ __forceinline__ float2 unpack2<__half>(uint32_t w) {
-  return __half22float2(*reinterpret_cast<const __half2*>(&w));
-}
-template <>
-__device__ __forceinline__ float2 unpack2<__nv_bfloat16>(uint32_t w) {
-  return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w));
-}
-template <typename S>
-__device__ __forceinline__ uint32_t pack2_rn(float lo, float hi);
-template <>
-__device__ __forceinline__ uint32_t pack2_rn<__half>(float lo, float hi) {
-  const __half2 h = __floats2half2_rn(lo, hi);
-  return *reinterpret_cast<const uint32_t*>(&h);
-}
-template <>
-__device__ __forceinline__ uint32_t pack2_rn<__nv_bfloat16>(float lo, float hi) {
-  const __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
-  return *reinterpret_cast<const uint32_t*>(&h);
-}
-
-template <typename S, bool SKIP_EDGES, bool VH, bool MASKSTORE>
-__device__ __forceinline__ void step_tile16(const DevGeom& g, const Co<float>& c, const S* __restrict__ src,
-                                            S* __restrict__ dst, int y, int xw, int lane, uint32_t seed,
-                                            int stochastic, bool mixed) {
-  constexpr int V = 4;
-  const int x0 = xw + lane * V;
-  const long long plane = g.plane;
-  int ym = y - 1, yp = y + 1;
-  if (g.py) {
-    ym = ym < 0 ? g.ny - 1 : ym;
-    yp = yp >= g.ny ? 0 : yp;
-  } else {
-    ym = ym < 0 ? 0 : ym;
-    yp = yp >= g.ny ? g.ny - 1 : yp;
-  }
-  const int xl = x0 > 0 ? x0 - 1 : 0;
-  const int xr = x0 + V < g.pitch ? x0 + V : g.pitch - 1;
-  const unsigned short* raw = reinterpret_cast<const unsigned short*>(src);
-  uint32_t w[14][2];  // nodes (x0, x0 + 1) and (x0 + 2, x0 + 3) of each plane, low half first
-#pragma unroll
-  for (int q = 0; q < 14; ++q) {
-    const int dir = q < 9 ? q : q - 9;
-    const int ex = ex_of(dir), ey = ey_of(dir);
-    const int row = ey > 0 ? ym : (ey < 0 ? yp : y);
-    const long long boff = q * plane + (long long)row * g.pitch;
-    const uint2 t = *reinterpret_cast<const uint2*>(raw + boff + x0);
-    if (ex == 0) {
-      w[q][0] = t.x;
-      w[q][1] = t.y;
-    } else if (ex > 0) {  // node k takes x0 + k - 1
-      uint32_t prev = __shfl_up_sync(0xffffffffu, t.y, 1);
-      if (lane == 0) prev = (uint32_t)raw[boff + xl] << 16;
-      w[q][0] = __byte_perm(prev, t.x, 0x5432);
-      w[q][1] = __byte_perm(t.x, t.y, 0x5432);
-    } else {  // node k takes x0 + k + 1
-      uint32_t next = __shfl_down_sync(0xffffffffu, t.x, 1);
-      if (lane == 31) next = (uint32_t)raw[boff + xr];
-      w[q][0] = __byte_perm(t.x, t.y, 0x5432);
-      w[q][1] = __byte_perm(t.y, next, 0x5432);
-    }
-  }
-  const uint32_t key = stochastic ? sr_key(seed, (long long)(y + g.yoff) * g.pitch + x0) : 0u;
-  uint32_t qvw[2] = {0u, 0u};
-#pragma unroll
-  for (int pr = 0; pr < 2; ++pr) {
-    float d0[9], h0[5], d1[9], h1[5];
-#pragma unroll
-    for (int q = 0; q < 14; ++q) {
-      const float2 f = unpack2<S>(w[q][pr]);
-      if (q < 9) {
-        d0[q] = f.x;
-        d1[q] = f.y;
-      } else {
-        h0[q - 9] = f.x;
-        h1[q - 9] = f.y;
-      }
-    }
-    float qv0, qv1;
-    collide<float, VH>(c, d0, h0, qv0);
-    collide<float, VH>(c, d1, h1, qv1);
-    if constexpr (VH) qvw[pr] = pack2_rn<S>(qv0, qv1);
-#pragma unroll
-    for (int q = 0; q < 14; ++q) {
-      const float a = q < 9 ? d0[q] : h0[q - 9];
-      const float b = q < 9 ? d1[q] : h1[q - 9];
-      if (stochastic) {
-        uint32_t r0, r1;
-        sr_words(key, q, r0, r1);
-        w[q][pr] = cvt_rs2<S>(a, b, pr ? r1 : r0);
-      } else {
-        w[q][pr] = pack2_rn<S>(a, b);
-      }
-    }
-  }
-  unsigned short* out = reinterpret_cast<unsigned short*>(dst) + (long long)y * g.pitch + x0;
-  // nodes left to the boundary update: flagged nodes of a mixed tile and the edge columns
-  uint32_t skip = 0;
-  if constexpr (MASKSTORE) {
-    if (mixed) {
-      const uint16_t* fp = g.flags + (long long)y * g.pitch + x0;
-#pragma unroll
-      for (int k = 0; k < V; ++k)
-        if (fp[k] != 0 || x0 + k == 0 || x0 + k == g.nx - 1) skip |= 1u << k;
-    }
-  }
-  if constexpr (SKIP_EDGES) {
-#pragma unroll
-    for (int k = 0; k < V; ++k)
-      if (x0 + k == 0 || x0 + k == g.nx - 1) skip |= 1u << k;
-  }
-  if (skip) {
-#pragma unroll
-    for (int k = 0; k < V; ++k) {
-      if ((skip >> k) & 1u) continue;
-      const int sh = (k & 1) * 16;
-      if constexpr (VH) out[14 * plane + k] = (unsigned short)(qvw[k >> 1] >> sh);
-#pragma unroll
-      for (int q = 0; q < 14; ++q) out[q * plane + k] = (unsigned short)(w[q][k >> 1] >> sh);
-    }
-    return;
-  }
-  if constexpr (VH) *reinterpret_cast<uint2*>(out + 14 * plane) = make_uint2(qvw[0], qvw[1]);
-#pragma unroll
-  for (int q = 0; q < 14; ++q) *reinterpret_cast<uint2*>(out + q * plane) = make_uint2(w[q][0], w[q][1]);
-}
-
 template <typename S, int V, bool SKIP_EDGES = false, bool VH = false, bool SKIP_DEAD = true,
           bool MASKSTORE = false>
 __device__ __forceinline__ void step_tile(const DevGeom& g, const Co<typename Traits<S>::R>& c,
@@ -805,10 +670,6 @@ __device__ __forceinline__ void step_tile(const DevGeom& g, const Co<typename Tr
                                           int xw, int lane, uint32_t seed, int stochastic,
                                           bool mixed = false) {
   using R = typename Traits<S>::R;
-  if constexpr (sizeof(S) == 2 && V == 4 && !SKIP_DEAD) {
-    step_tile16<S, SKIP_EDGES, VH, MASKSTORE>(g, c, src, dst, y, xw, lane, seed, stochastic, mixed);
-    return;
-  }
   const int x0 = xw + lane * V;
   const long long plane = g.plane;
 

@@ -97,16 +97,13 @@ struct LoadIm2colT {
   }
 };
 
-// C(m = channel, n = pixel) into an activation view, with bias / ReLU / accumulate;
-// nhwc (optional) receives the result rounded to BF16 in the NHWC copy of the
-// same buffer (pixel-major, the layout the next convolution's gather reads).
+// C(m = channel, n = pixel) into an activation view, with bias / ReLU / accumulate.
 struct StoreAct {
   float* base;
   int cs, coff, H, W;
   const float* bias;
   int relu, accumulate;
-  __nv_bfloat16* nhwc;
-  __device__ __forceinline__ float value(int m, int n, float v) const {
+  __device__ __forceinline__ void operator()(int m, int n, float v) const {
     const int hw = H * W;
     const int nb = n / hw, p = n - nb * hw;
     float* dst = base + ((long long)nb * cs + coff + m) * hw + p;
@@ -114,11 +111,6 @@ struct StoreAct {
     if (relu) v = v > 0.0f ? v : 0.0f;
     if (accumulate) v += *dst;
     *dst = v;
-    return v;
-  }
-  __device__ __forceinline__ void operator()(int m, int n, float v) const {
-    v = value(m, n, v);
-    if (nhwc) nhwc[(long long)n * cs + coff + m] = __float2bfloat16_rn(v);
   }
 };
 
@@ -210,60 +202,6 @@ struct GatherIm2col {
         put_chunk(dst, r, kc, v);
       }
     }
-  }
-};
-
-// BF16 NHWC copy of an activation buffer: sample n, pixel (y, x), channel
-// coff + c at base[((n H + y) W + x) cs + coff + c].
-struct ActB {
-  const __nv_bfloat16* base;
-  int cs, coff, C, H, W;
-};
-
-// GatherIm2col from the BF16 NHWC copy (C, cs and coff multiples of 8): each
-// 16-byte chunk of a row is one tap's eight channels, one 16-byte load, already
-// in BF16 (the same roundings as gathering the FP32 activations).
-template <int KS>
-struct GatherIm2colB {
-  static constexpr bool kBulk = false;
-  ActB x;
-  __device__ __forceinline__ void operator()(uint8_t* dst, int row0, int rows_valid, int, int k0,
-                                             int kend) const {
-    constexpr int KK = KS * KS, R = KS / 2;
-    const int r = threadIdx.x;
-    const int hw = x.H * x.W, C = x.C;
-    const bool rv = r < rows_valid;
-    int nb = 0, yy = 0, xx = 0;
-    if (rv) {
-      const int m = row0 + r;
-      nb = m / hw;
-      const int p = m - nb * hw;
-      yy = p / x.W;
-      xx = p - yy * x.W;
-    }
-    uint32_t vm = 0;  // taps inside the image
-#pragma unroll
-    for (int t = 0; t < KK; ++t) {
-      const int sy = yy + t / KS - R, sx = xx + t % KS - R;
-      if (rv && sy >= 0 && sy < x.H && sx >= 0 && sx < x.W) vm |= 1u << t;
-    }
-    const __nv_bfloat16* src = x.base + (((long long)nb * x.H + yy) * x.W + xx) * x.cs + x.coff;
-    int t = k0 / C, c = k0 - t * C;
-    uint4 v[tc::kBK / 8];
-#pragma unroll
-    for (int kc = 0; kc < tc::kBK / 8; ++kc) {
-      const bool ok = k0 + kc * 8 < kend && ((vm >> t) & 1u);
-      const long long off = ((long long)(t / KS - R) * x.W + (t % KS - R)) * x.cs + c;
-      v[kc] = ok ? __ldg(reinterpret_cast<const uint4*>(src + off)) : make_uint4(0u, 0u, 0u, 0u);
-      c += 8;
-      if (c == C) {
-        c = 0;
-        ++t;
-      }
-    }
-#pragma unroll
-    for (int kc = 0; kc < tc::kBK / 8; ++kc)
-      *reinterpret_cast<uint4*>(dst + tc::chunk_off(r, kc)) = v[kc];
   }
 };
 
@@ -375,30 +313,9 @@ struct GatherRows {
   }
 };
 
-// Tensor-core epilogue stores: row16 takes columns n .. n + cnt - 1 (cnt <= 16)
-// of one accumulator row m.
 struct TStoreAct {  // D(m = pixel, n = channel)
   StoreAct s;
   __device__ __forceinline__ void operator()(int m, int n, float v, int) const { s(n, m, v); }
-  __device__ __forceinline__ void row16(int m, int n, const float (&v)[16], int cnt, int) const {
-    float o[16];
-#pragma unroll
-    for (int j = 0; j < 16; ++j)
-      if (j < cnt) o[j] = s.value(n + j, m, v[j]);
-    if (!s.nhwc) return;
-    __nv_bfloat16* d = s.nhwc + (long long)m * s.cs + s.coff + n;
-    if (cnt == 16 && ((s.cs | (s.coff + n)) & 7) == 0) {  // two 16-byte stores
-      uint4* d4 = reinterpret_cast<uint4*>(d);
-      d4[0] = make_uint4(tc::pack_bf16(o[0], o[1]), tc::pack_bf16(o[2], o[3]), tc::pack_bf16(o[4], o[5]),
-                         tc::pack_bf16(o[6], o[7]));
-      d4[1] = make_uint4(tc::pack_bf16(o[8], o[9]), tc::pack_bf16(o[10], o[11]),
-                         tc::pack_bf16(o[12], o[13]), tc::pack_bf16(o[14], o[15]));
-    } else {
-#pragma unroll
-      for (int j = 0; j < 16; ++j)
-        if (j < cnt) d[j] = __float2bfloat16_rn(o[j]);
-    }
-  }
 };
 struct TStoreSplit {  // D(m = pixel, n = channel) of split z -> part[z][n][m]
   float* part;
@@ -406,20 +323,10 @@ struct TStoreSplit {  // D(m = pixel, n = channel) of split z -> part[z][n][m]
   __device__ __forceinline__ void operator()(int m, int n, float v, int z) const {
     part[((long long)z * N + n) * M + m] = v;
   }
-  __device__ __forceinline__ void row16(int m, int n, const float (&v)[16], int cnt, int z) const {
-#pragma unroll
-    for (int j = 0; j < 16; ++j)
-      if (j < cnt) (*this)(m, n + j, v[j], z);
-  }
 };
 struct TStorePartial {  // D(m = (ci, tap), n = co) of split z
   StorePartial s;
   __device__ __forceinline__ void operator()(int m, int n, float v, int z) const { s(n, m, v, z); }
-  __device__ __forceinline__ void row16(int m, int n, const float (&v)[16], int cnt, int z) const {
-#pragma unroll
-    for (int j = 0; j < 16; ++j)
-      if (j < cnt) s(n + j, m, v[j], z);
-  }
 };
 
 // Pre-packed BF16 weights for the tensor-core GEMMs (tc::Packed layout), one
@@ -612,8 +519,7 @@ __global__ void relu_back_kernel(Act y, float* __restrict__ g, int gcs, int gcof
 }
 
 // 2x2 average pool: out (H/2 x W/2) from in; backward adds g_out/4 to the four inputs
-__global__ void pool_kernel(Act in, float* __restrict__ out, int ocs, int ocoff, int N,
-                            __nv_bfloat16* __restrict__ onhwc) {
+__global__ void pool_kernel(Act in, float* __restrict__ out, int ocs, int ocoff, int N) {
   const int Wo = in.W / 2, ho = (in.H / 2) * Wo, hw = in.H * in.W;
   for (int pc = blockIdx.y; pc < N * in.C; pc += gridDim.y) {
     const int nb = pc / in.C, c = pc - nb * in.C;
@@ -622,9 +528,7 @@ __global__ void pool_kernel(Act in, float* __restrict__ out, int ocs, int ocoff,
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < ho; p += gridDim.x * blockDim.x) {
       const int y = p / Wo, x = p - y * Wo;
       const float* q = ip + 2 * y * in.W + 2 * x;
-      const float v = 0.25f * ((q[0] + q[1]) + (q[in.W] + q[in.W + 1]));
-      op[p] = v;
-      if (onhwc) onhwc[((long long)nb * ho + p) * ocs + ocoff + c] = __float2bfloat16_rn(v);
+      op[p] = 0.25f * ((q[0] + q[1]) + (q[in.W] + q[in.W + 1]));
     }
   }
 }
@@ -654,56 +558,6 @@ __global__ void up_kernel(Act in, float* __restrict__ out, int ocs, int ocoff, i
     }
   }
 }
-// The NHWC copy of a nearest 2x upsample: 16-byte chunks (eight channels) of the
-// input's NHWC copy to the four output pixels of each input pixel.
-__global__ void up_nhwc_kernel(const __nv_bfloat16* __restrict__ in, int ics, int C, int Hi, int Wi,
-                               __nv_bfloat16* __restrict__ out, int ocs, int ocoff, int N) {
-  const int C8 = C / 8, W = 2 * Wi;
-  const long long total = (long long)N * 4 * Hi * Wi * C8;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
-       i += (long long)gridDim.x * blockDim.x) {
-    const int cg = (int)(i % C8);
-    const long long op = i / C8;  // output pixel over all samples
-    const int x = (int)(op % W);
-    const long long r = op / W;
-    const int y = (int)(r % (2 * Hi));
-    const long long nb = r / (2 * Hi);
-    const uint4 v = *reinterpret_cast<const uint4*>(in + ((nb * Hi + (y >> 1)) * Wi + (x >> 1)) * ics + cg * 8);
-    *reinterpret_cast<uint4*>(out + op * ocs + ocoff + cg * 8) = v;
-  }
-}
-
-// ReLU backward with the NHWC copy of the result: thread (pixel, group of eight
-// channels) masks g in place (FP32 NCHW) and writes the eight values as one
-// 16-byte BF16 chunk of the gradient's NHWC copy.
-__global__ void relu_back8_kernel(Act y, float* __restrict__ g, int gcs, int gcoff, int N,
-                                  __nv_bfloat16* __restrict__ gnhwc) {
-  const int hw = y.H * y.W, C8 = y.C / 8;
-  const long long total = (long long)N * C8 * hw;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
-       i += (long long)gridDim.x * blockDim.x) {
-    const int p = (int)(i % hw);
-    const long long r = i / hw;
-    const int cg = (int)(r % C8);
-    const long long nb = r / C8;
-    float v[8];
-#pragma unroll
-    for (int e = 0; e < 8; ++e) {
-      const int c = cg * 8 + e;
-      const float yv = y.base[(nb * y.cs + y.coff + c) * hw + p];
-      float* gp = g + (nb * gcs + gcoff + c) * hw + p;
-      v[e] = *gp;
-      if (!(yv > 0.0f)) {
-        v[e] = 0.0f;
-        *gp = 0.0f;
-      }
-    }
-    *reinterpret_cast<uint4*>(gnhwc + (nb * hw + p) * gcs + gcoff + cg * 8) =
-        make_uint4(tc::pack_bf16(v[0], v[1]), tc::pack_bf16(v[2], v[3]), tc::pack_bf16(v[4], v[5]),
-                   tc::pack_bf16(v[6], v[7]));
-  }
-}
-
 __global__ void up_back_kernel(Act gout, float* __restrict__ gin, int gcs, int gcoff, int N) {
   const int Wi = gout.W / 2, hi = (gout.H / 2) * Wi, hw = gout.H * gout.W;
   for (int pc = blockIdx.y; pc < N * gout.C; pc += gridDim.y) {
@@ -851,10 +705,6 @@ struct clbm_net {
   std::vector<PackDesc> pack;                  // [2 * layer + transpose]
   long long packed_max = 0;
   std::vector<float*> act, gact;               // per buffer
-  // BF16 NHWC copies (tensor-core math, buffers whose channel count is a multiple
-  // of 8; nullptr otherwise): activations written by the producing convolution,
-  // pooling and upsampling, activation gradients by the ReLU backward
-  std::vector<__nv_bfloat16*> actb, gactb;
   std::vector<int> act_c, act_hw;              // channels and H (= W) of each buffer
   float* part = nullptr;                       // split-K partials
   long long part_cap = 0;
@@ -908,17 +758,6 @@ Act view(clbm_net* net, int id, int coff, int C, bool grad = false) {
 
 bool tensor_math(const clbm_net* net) { return net->cfg.math == CLBM_NET_TENSOR; }
 
-// The NHWC copy of a view, if the buffer has one and the view's channels line
-// up with 16-byte chunks (else base = nullptr: gather the FP32 activations).
-ActB view_b(const clbm_net* net, const Act& a, bool grad) {
-  ActB b{nullptr, a.cs, a.coff, a.C, a.H, a.W};
-  const std::vector<float*>& f = grad ? net->gact : net->act;
-  const std::vector<__nv_bfloat16*>& v = grad ? net->gactb : net->actb;
-  for (size_t id = 0; id < f.size(); ++id)
-    if (f[id] == a.base && id < v.size() && v[id] && ((a.cs | a.coff | a.C) & 7) == 0) b.base = v[id];
-  return b;
-}
-
 // D[M][N] (+ split-K along z) on the tensor cores
 template <class GA, class GB, class ST>
 cudaError_t tc_gemm(clbm_net* net, GA ga, GB gb, ST st, int M, int N, int K, int kper) {
@@ -951,26 +790,18 @@ int conv_splits(int sms, int M, int N, int K) {
 
 // Implicit-im2col forward or input-gradient GEMM; split GEMMs finish in
 // splitk_finish_kernel.
-template <class GA, class GB>
-cudaError_t tc_conv_gemm_g(clbm_net* net, GA ga, GB gb, StoreAct st, int M, int N, int K) {
+template <int KS, class GB>
+cudaError_t tc_conv_gemm(clbm_net* net, Act x, GB gb, StoreAct st, int M, int N, int K) {
   const int splits = conv_splits(net->sms, M, N, K);
-  if (splits == 1) return tc_gemm(net, ga, gb, TStoreAct{st}, M, N, K, K);
+  if (splits == 1) return tc_gemm(net, GatherIm2col<KS>{x}, gb, TStoreAct{st}, M, N, K, K);
   if ((long long)splits * M * N > net->part_cap) return cudaErrorInvalidValue;
   const int kper = (K + splits - 1) / splits;
   const int kp = (kper + tc::kBK - 1) / tc::kBK * tc::kBK;
-  cudaError_t e = tc_gemm(net, ga, gb, TStoreSplit{net->part, M, N}, M, N, K, kp);
+  cudaError_t e = tc_gemm(net, GatherIm2col<KS>{x}, gb, TStoreSplit{net->part, M, N}, M, N, K, kp);
   if (e) return e;
   splitk_finish_kernel<<<dim3((unsigned)std::min((M + 255) / 256, 64), (unsigned)std::min(N, 65535)), 256, 0, net->stream>>>(
       net->part, (K + kp - 1) / kp, M, N, st);
   return cudaGetLastError();
-}
-
-// The forward / input-gradient GEMM of a KS x KS convolution: gathers the BF16
-// NHWC copy when there is one, else the FP32 activations.
-template <int KS, class GB>
-cudaError_t tc_conv_gemm(clbm_net* net, Act x, ActB xb, GB gb, StoreAct st, int M, int N, int K) {
-  if (xb.base) return tc_conv_gemm_g(net, GatherIm2colB<KS>{xb}, gb, st, M, N, K);
-  return tc_conv_gemm_g(net, GatherIm2col<KS>{x}, gb, st, M, N, K);
 }
 
 // Refresh the packed weight tiles from the BF16 weights (one launch, all layers).
@@ -1006,13 +837,11 @@ cudaError_t conv_forward(clbm_net* net, const Conv& cv, Act x, int out_id, int o
   const int M = cv.co, Kd = cv.ci * cv.ks * cv.ks, Np = N * cv.H * cv.W;
   LoadW la{net->pb + cv.w_off, Kd};
   LoadIm2col lb{x, cv.ks};
-  StoreAct st{net->act[out_id], net->act_c[out_id], out_coff, cv.H, cv.W, net->p + cv.b_off, relu, 0, nullptr};
+  StoreAct st{net->act[out_id], net->act_c[out_id], out_coff, cv.H, cv.W, net->p + cv.b_off, relu, 0};
   if (tensor_math(net)) {  // D(pixel, co) = sum_k im2col(x)(pixel, k) W(co, k)
-    st.nhwc = net->actb[out_id];
     const tc::Packed w = packed_of(net, cv.index, 0);
-    const ActB xb = view_b(net, x, false);
-    if (cv.ks == 3) return tc_conv_gemm<3>(net, x, xb, w, st, Np, M, Kd);
-    return tc_conv_gemm<1>(net, x, xb, w, st, Np, M, Kd);
+    if (cv.ks == 3) return tc_conv_gemm<3>(net, x, w, st, Np, M, Kd);
+    return tc_conv_gemm<1>(net, x, w, st, Np, M, Kd);
   }
   dim3 grid((Np + BN - 1) / BN, (M + BM - 1) / BM, 1);
   gemm_kernel<<<grid, GT, 0, net->stream>>>(la, lb, st, M, Np, Kd, Kd);
@@ -1053,13 +882,12 @@ cudaError_t conv_backward(clbm_net* net, const Conv& cv, Act x, Act gy, int gx_i
   }
   if (gx_id >= 0) {  // input gradient: M = ci, N = pixels, K = co*t, with flipped weights
     const int kk = cv.ks * cv.ks;
-    StoreAct st{net->gact[gx_id], net->act_c[gx_id], gx_coff, cv.H, cv.W, nullptr, 0, 1, nullptr};
+    StoreAct st{net->gact[gx_id], net->act_c[gx_id], gx_coff, cv.H, cv.W, nullptr, 0, 1};
     if (tensor_math(net)) {  // D(pixel, ci) = sum_k im2col(gy)(pixel, k) W'(ci, k)
       const tc::Packed w = packed_of(net, cv.index, 1);
       const int K = cv.co * kk;
-      const ActB gyb = view_b(net, gy, true);
-      if (cv.ks == 3) return tc_conv_gemm<3>(net, gy, gyb, w, st, Np, cv.ci, K);
-      return tc_conv_gemm<1>(net, gy, gyb, w, st, Np, cv.ci, K);
+      if (cv.ks == 3) return tc_conv_gemm<3>(net, gy, w, st, Np, cv.ci, K);
+      return tc_conv_gemm<1>(net, gy, w, st, Np, cv.ci, K);
     }
     flip_kernel<<<grid1((long long)cv.co * cv.ci * kk), 256, 0, net->stream>>>(
         net->pb + cv.w_off, net->pt + cv.w_off, cv.co, cv.ci, cv.ks);
@@ -1073,12 +901,6 @@ cudaError_t conv_backward(clbm_net* net, const Conv& cv, Act x, Act gy, int gx_i
 
 cudaError_t relu_back(clbm_net* net, int id, int coff, int C, int N) {
   Act y = view(net, id, coff, C);
-  if (net->gactb[id] && ((net->act_c[id] | coff | C) & 7) == 0) {
-    const long long n = (long long)N * (C / 8) * y.H * y.W;
-    relu_back8_kernel<<<grid1(n), 256, 0, net->stream>>>(y, net->gact[id], net->act_c[id], coff, N,
-                                                         net->gactb[id]);
-    return cudaGetLastError();
-  }
   relu_back_kernel<<<plane_grid(y.H * y.W, (long long)N * C), 256, 0, net->stream>>>(
       y, net->gact[id], net->act_c[id], coff, N);
   return cudaGetLastError();
@@ -1096,7 +918,7 @@ cudaError_t forward(clbm_net* net, const Plan& P, int N) {
     if ((e = conv_forward(net, net->convs[ci++], view(net, P.a1[l], 0, c), P.cat[l], cup, 1, N))) return e;
     Act skip = view(net, P.cat[l], cup, c);
     pool_kernel<<<plane_grid((skip.H / 2) * (skip.W / 2), (long long)N * c), 256, 0, net->stream>>>(
-        skip, net->act[P.pool[l]], c, 0, N, net->actb[P.pool[l]]);
+        skip, net->act[P.pool[l]], c, 0, N);
     x = view(net, P.pool[l], 0, c);
   }
   const int cb = B << (L - 1);
@@ -1107,13 +929,6 @@ cudaError_t forward(clbm_net* net, const Plan& P, int N) {
     const int c = B << l, cup = B << (l + 1);
     up_kernel<<<plane_grid(prev.H * 2 * prev.W * 2, (long long)N * cup), 256, 0, net->stream>>>(
         prev, net->act[P.cat[l]], net->act_c[P.cat[l]], 0, N);
-    if (net->actb[P.cat[l]]) {  // the upsampled part of the concatenation's NHWC copy
-      const ActB pb = view_b(net, prev, false);
-      if (!pb.base) return cudaErrorInvalidValue;
-      const long long n = (long long)N * 4 * prev.H * prev.W * (cup / 8);
-      up_nhwc_kernel<<<grid1(n), 256, 0, net->stream>>>(pb.base, pb.cs, cup, prev.H, prev.W,
-                                                         net->actb[P.cat[l]], net->act_c[P.cat[l]], 0, N);
-    }
     if ((e = conv_forward(net, net->convs[ci++], view(net, P.cat[l], 0, cup + c), P.d1[l], 0, 1, N))) return e;
     if ((e = conv_forward(net, net->convs[ci++], view(net, P.d1[l], 0, c), P.d2[l], 0, 1, N))) return e;
     prev = view(net, P.d2[l], 0, c);
@@ -1227,8 +1042,6 @@ clbm_status clbm_net_destroy(clbm_net* n) {
   cudaFree(n->pt);
   for (float* a : n->act) cudaFree(a);
   for (float* a : n->gact) cudaFree(a);
-  for (__nv_bfloat16* a : n->actb) cudaFree(a);
-  for (__nv_bfloat16* a : n->gactb) cudaFree(a);
   cudaFree(n->part);
   cudaFree(n->loss_part);
   if (n->tflag) cudaFreeHost(n->tflag);
@@ -1336,15 +1149,6 @@ clbm_status clbm_net_create(const clbm_net_config* cfg, uint64_t seed, void* str
     }
     n->act.push_back(a);
     n->gact.push_back(ga);
-    __nv_bfloat16 *ab = nullptr, *gab = nullptr;
-    if (c.math == CLBM_NET_TENSOR && n->act_c[id] % 8 == 0) {
-      if (cudaMalloc(&ab, e * sizeof(__nv_bfloat16)) || cudaMalloc(&gab, e * sizeof(__nv_bfloat16))) {
-        cudaFree(ab);
-        return bail(CLBM_ENOMEM);
-      }
-    }
-    n->actb.push_back(ab);
-    n->gactb.push_back(gab);
   }
   {  // one wave of CTAs is sized from the device's multiprocessor count
     int dev = 0, sms = 0;

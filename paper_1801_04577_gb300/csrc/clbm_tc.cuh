@@ -13,8 +13,7 @@
 // them to the slice's mbarrier; the stage is refilled only after that barrier
 // fires, so the gather of slice i+1 overlaps the MMAs of slice i.  The
 // epilogue reads the accumulator with tcgen05.ld (warp w owns lanes
-// 32w..32w+31) and hands each row's 16 columns at a time to the store functor
-// (st.row16).
+// 32w..32w+31) and hands every element to the store functor.
 //
 // The B operand can instead be pre-packed in global memory in exactly that
 // layout and moved per slice by one cp.async.bulk copy (Packed).
@@ -301,7 +300,11 @@ __global__ void __launch_bounds__(kThreads) gemm_kernel(GA ga, GB gb, ST st, int
 #pragma unroll
         for (int j = 0; j < 16; ++j) v[j] = 0.0f;
       }
-      if (r < mvalid && c0 < nvalid) st.row16(m, n0 + c0, v, min(16, nvalid - c0), (int)blockIdx.z);
+      if (r < mvalid) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+          if (c0 + j < nvalid) st(m, n0 + c0 + j, v[j], (int)blockIdx.z);
+      }
     }
   }
   fence_before();

@@ -126,33 +126,3 @@ def test_rb_time_averaged_nusselt(precision, tol):
     got = mean_nu(clbm.from_workload(w, precision))
     assert abs(got - ref) <= tol * abs(ref), (got, ref)
 
-
-@pytest.mark.parametrize("precision,rounding", [("f16", 0), ("f16", 1), ("bf16", 0), ("bf16", 1)])
-@pytest.mark.parametrize("name", ["rb", "obstacle", "viscous"])
-def test_16bit_single_lattice_path_equals_batch_path(precision, rounding, name):
-    """Single 16-bit lattices run the register-packed tile path (raw 16-bit
-    pairs shifted by byte permutation, unpacked two nodes at a time); batched
-    lattices the generic one.  Same roundings, same stochastic bits: the fields
-    must agree bit for bit.  (Batches have no viscous source: that case checks
-    the packed path's 15th plane through graph replay against single launches.)"""
-    if name == "rb":
-        w = I.rayleigh_benard(300, 70, Ra=1e5, Q=1e-4, noise=1e-2)
-        w.init = I.random_fields(300, 70, seed=41, amp=0.02)
-    elif name == "obstacle":
-        w = I.obstacle_channel(261, 37)
-    else:
-        w = I.natural_convection_cavity(70, 1e5)
-        w.params.viscous_heating = 1
-    s = clbm.from_workload(w, precision, rounding=rounding)
-    s.step(100)
-    if name == "viscous":  # batches run without the viscous source: compare two single runs
-        t = clbm.from_workload(w, precision, rounding=rounding)
-        for _ in range(100):
-            t.step(1)
-        ref = t.moments()
-    else:
-        b = clbm.Batch([w], precision, rounding=rounding, autotune=False)
-        b.solve(0.0, 100, check_every=100)
-        ref = b.moments(0)
-    for a, r in zip(s.moments(), ref):
-        np.testing.assert_array_equal(a, r)
