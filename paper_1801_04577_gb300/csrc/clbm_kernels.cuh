@@ -208,16 +208,17 @@ __device__ __forceinline__ void stv_sr(S* p, const float (&o)[V], uint32_t r0, u
 
 // The random bits of a store depend on the step, the node and the plane only,
 // whichever kernel updates the node: one key per group of four nodes x0 = x & ~3
-// of a row (the full mixer of step and node), and per plane two words from one
-// multiply-xorshift of the key and a golden-ratio multiple of the plane, and one
-// more; word 0 rounds nodes x0, x0 + 1 (low, high half), word 1 nodes x0 + 2, x0 + 3.
+// of a row (the full mixer of step and node), and per plane two words: one
+// multiply-xorshift of the key plus a golden-ratio multiple of the plane, and one
+// more multiply-xorshift of that word; word 0 rounds nodes x0, x0 + 1 (low, high
+// half), word 1 nodes x0 + 2, x0 + 3.
 __device__ __forceinline__ uint32_t sr_key(uint32_t seed, long long group_node) {
   return seed ^ mix32((uint32_t)group_node);
 }
 __device__ __forceinline__ void sr_words(uint32_t key, int q, uint32_t& r0, uint32_t& r1) {
-  r0 = (key ^ (0x9E3779B9u * (uint32_t)(q + 1))) * 0x7feb352du;
+  r0 = (key + 0x9E3779B9u * (uint32_t)(q + 1)) * 0x7feb352du;
   r0 ^= r0 >> 15;
-  r1 = (r0 ^ 0x85EBCA6Bu) * 0x846ca68bu;
+  r1 = r0 * 0x846ca68bu;
   r1 ^= r1 >> 16;
 }
 
@@ -283,6 +284,12 @@ __host__ __device__ __forceinline__ void fwd1(R am, R a0, R ap, R u, R& c0, R& c
   c1 = s - u * c0;
   c2 = (ap + am) - (u + u) * s + u * u * c0;
 }
+// The same from the row's sum c0, difference ap - am and sum ap + am.
+template <typename R>
+__host__ __device__ __forceinline__ void fwd1p(R c0, R s, R q, R u, R& c1, R& c2) {
+  c1 = s - u * c0;
+  c2 = q - (u + u) * s + u * u * c0;
+}
 template <typename R>
 __host__ __device__ __forceinline__ void inv1(R c0, R c1, R c2, R u, R& am, R& a0, R& ap) {
   const R r1 = c1 + u * c0;
@@ -303,15 +310,20 @@ template <typename R, bool VH = false>
 __host__ __device__ __forceinline__ void collide(const Co<R>& c, R (&d)[9], R (&h)[5], R& qv) {
   const R third = R(1.0 / 3.0);
   // Eq. 25 (T - T0 = sum h + Q/2) and Eq. 2
-  const R sh = (h[0] + h[1]) + (h[2] + h[3]) + h[4];
+  const R k20 = h[1] + h[3], k02 = h[2] + h[4];
+  const R sh = (h[0] + k20) + k02;
   const R dT = sh + c.hQ;
   const R Fx = c.Fvx;
   const R Fy = c.Fvy + c.rgb * dT;
-  // Eq. 12 (sum_i w_i e_i = 0, so the rest state adds nothing to j)
-  const R drho = ((d[0] + d[1]) + (d[2] + d[3])) + ((d[4] + d[5]) + (d[6] + d[7])) + d[8];
+  // Eq. 12 (sum_i w_i e_i = 0, so the rest state adds nothing to j), from the
+  // sums and differences of each velocity row, which the x-pass below reuses
+  const R m0 = (d[7] + d[4]) + d[8], ms = d[8] - d[7], mq = d[8] + d[7];  // e_y = -1
+  const R z0 = (d[3] + d[0]) + d[1], zs = d[1] - d[3], zq = d[1] + d[3];  // e_y =  0
+  const R p0 = (d[6] + d[2]) + d[5], ps = d[5] - d[6], pq = d[5] + d[6];  // e_y = +1
+  const R drho = (m0 + z0) + p0;
   const R rho = c.rho0 + drho;
-  const R jx = (d[1] - d[3]) + (d[5] - d[6]) + (d[8] - d[7]);
-  const R jy = (d[2] - d[4]) + (d[5] - d[7]) + (d[6] - d[8]);
+  const R jx = (ms + zs) + ps;
+  const R jy = p0 - m0;
   // FP32: the reciprocal to within 2 ulp (hardware approximation), which the
   // FP32 parity bound leaves ample room for; FP64: the exact quotient
   R inv_rho = R(1) / rho;
@@ -322,12 +334,13 @@ __host__ __device__ __forceinline__ void collide(const Co<R>& c, R (&d)[9], R (&
   const R uy = (jy + R(0.5) * Fy) * inv_rho;
 
   // central moments of the deviations: x-pass per velocity row, then y-pass
-  R xm0, xm1, xm2, xz0, xz1, xz2, xp0, xp1, xp2;
-  fwd1(d[7], d[4], d[8], ux, xm0, xm1, xm2);  // e_y = -1
-  fwd1(d[3], d[0], d[1], ux, xz0, xz1, xz2);  // e_y =  0
-  fwd1(d[6], d[2], d[5], ux, xp0, xp1, xp2);  // e_y = +1
-  R b00, b01, b02, b10, b11, b12, b20, b21, b22;
-  fwd1(xm0, xz0, xp0, uy, b00, b01, b02);
+  R xm1, xm2, xz1, xz2, xp1, xp2;
+  fwd1p(m0, ms, mq, ux, xm1, xm2);  // e_y = -1
+  fwd1p(z0, zs, zq, ux, xz1, xz2);  // e_y =  0
+  fwd1p(p0, ps, pq, ux, xp1, xp2);  // e_y = +1
+  R b01, b02, b10, b11, b12, b20, b21, b22;
+  const R b00 = drho;
+  fwd1p(drho, jy, p0 + m0, uy, b01, b02);
   fwd1(xm1, xz1, xp1, uy, b10, b11, b12);
   fwd1(xm2, xz2, xp2, uy, b20, b21, b22);
 
@@ -370,7 +383,6 @@ __host__ __device__ __forceinline__ void collide(const Co<R>& c, R (&d)[9], R (&
 
   // thermal (Eq. 15-20, 23-24) on deviations from w^T T0; kappa^T = (1, -u, cT2 + u^2)
   const R k10 = h[1] - h[3], k01 = h[2] - h[4];
-  const R k20 = h[1] + h[3], k02 = h[2] + h[4];
   const R t10 = k10 - ux * sh;
   const R t01 = k01 - uy * sh;
   const R t20 = k20 - (ux + ux) * k10 + ux2 * sh;
