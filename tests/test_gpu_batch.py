@@ -168,3 +168,21 @@ def test_batch_with_walls_off_the_link_midpoint():
         errs = compare(w, b.moments(i), s.moments())
         assert max(errs.values()) <= 1e-13, (w.name, errs)
     b.close()
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+def test_config4_generator_cavities_against_oracle(precision):
+    """Cavities of the 512-cavity generator (uneven sides, both orientations,
+    mixed Dirichlet / Neumann / Robin sides, heat sources, Ra up to 1e6; sides
+    32..40 here so the oracle stays quick) in one batch, each against the FP64
+    oracle after 1,000 steps, every field against its own largest value."""
+    ws = I.random_cavities(6, hmax=40)
+    b = clbm.Batch(ws, precision, autotune=True)
+    conv, _, steps = b.solve(0.0, 1000, check_every=500)
+    assert steps == 1000 and (conv == -1).all()
+    for i, w in enumerate(ws):
+        o = oracle.from_workload(w)
+        o.step(1000)
+        errs = compare(w, b.moments(i), o.moments())
+        assert max(errs.values()) <= TOL[precision], (w.name, errs)
+    b.close()
