@@ -105,7 +105,12 @@ def allreduce_sums(sums: np.ndarray, device=None, group=None) -> np.ndarray:
 
 class DistSlab:
     """One slab per process: the GPU slab of this rank, packed halo buffers on
-    its device, and the exchange through torch.distributed."""
+    its device, and the exchange through torch.distributed.  With NCCL the
+    packed rows travel between the GPUs directly; with gloo (whose send and
+    receive take host tensors) they are staged through pinned host memory, so
+    ranks may even share one GPU -- no kernel of one rank ever waits on another
+    rank: each rank's host finishes the exchange before it launches its next
+    step."""
 
     def __init__(self, w, precision: str = "f32", rounding: int = 0, stream: Optional[int] = None,
                  group=None):
@@ -115,20 +120,41 @@ class DistSlab:
         self.group = group
         self.rank = dist.get_rank(group) if dist.is_initialized() else 0
         self.world = dist.get_world_size(group) if dist.is_initialized() else 1
+        self.staged = dist.is_initialized() and dist.get_backend(group) == "gloo"
         self.periodic = bool(w.params.periodic_y)
         self.y0, self.rows = partition(w.params.ny, self.world)[self.rank]
+        # the library's work, the staging copies and the communication share one stream
+        if stream is None:
+            self.tstream = torch.cuda.Stream()
+            stream = self.tstream.cuda_stream
+        else:
+            self.tstream = torch.cuda.ExternalStream(stream)
         self.slab = clbm.Slab(w.params, self.y0, self.rows, w.geom, precision, stream, w.init, rounding)
         nbytes = clbm.clbm_halo_bytes(self.slab.ctx)
         dev = torch.device("cuda", torch.cuda.current_device())
         self.bufs = [torch.empty(nbytes, dtype=torch.uint8, device=dev) for _ in range(4)]
+        if self.staged:
+            self.host = [torch.empty(nbytes, dtype=torch.uint8).pin_memory() for _ in range(4)]
         self.exchange()
 
     def exchange(self):
+        import torch
         send_lo, send_hi, recv_lo, recv_hi = self.bufs
         below, above = neighbours(self.rank, self.world, self.periodic)
         clbm.clbm_halo_pack(self.slab.ctx, 0, send_lo)
         clbm.clbm_halo_pack(self.slab.ctx, 1, send_hi)
-        exchange(send_lo, send_hi, recv_lo, recv_hi, self.rank, self.world, self.periodic, self.group)
+        with torch.cuda.stream(self.tstream):
+            if self.staged:
+                hs_lo, hs_hi, hr_lo, hr_hi = self.host
+                hs_lo.copy_(send_lo, non_blocking=True)
+                hs_hi.copy_(send_hi, non_blocking=True)
+                self.tstream.synchronize()
+                exchange(hs_lo, hs_hi, hr_lo, hr_hi, self.rank, self.world, self.periodic, self.group)
+                recv_lo.copy_(hr_lo, non_blocking=True)
+                recv_hi.copy_(hr_hi, non_blocking=True)
+            else:
+                exchange(send_lo, send_hi, recv_lo, recv_hi, self.rank, self.world, self.periodic,
+                         self.group)
         if below is not None:
             clbm.clbm_halo_unpack(self.slab.ctx, 0, recv_lo)
         if above is not None:
@@ -139,14 +165,21 @@ class DistSlab:
             self.slab.step(1)
             self.exchange()
 
+    def _dev(self):
+        return None if self.staged else self.bufs[0].device
+
     def residual(self) -> float:
-        s = allreduce_sums(self.slab.sums(clbm.REDUCE_RESIDUAL), device=self.bufs[0].device, group=self.group)
+        s = allreduce_sums(self.slab.sums(clbm.REDUCE_RESIDUAL), device=self._dev(), group=self.group)
         return float(clbm.clbm_finish_sums(self.slab.ctx, clbm.REDUCE_RESIDUAL, s)[0])
 
     def nusselt(self, which: int, length: float, dT: float) -> float:
-        s = allreduce_sums(self.slab.sums(clbm.REDUCE_NUSSELT, which), device=self.bufs[0].device,
+        s = allreduce_sums(self.slab.sums(clbm.REDUCE_NUSSELT, which), device=self._dev(),
                            group=self.group)
         return float(clbm.clbm_finish_sums(self.slab.ctx, clbm.REDUCE_NUSSELT, s, length, dT)[0])
+
+    def totals(self) -> np.ndarray:
+        s = allreduce_sums(self.slab.sums(clbm.REDUCE_TOTALS), device=self._dev(), group=self.group)
+        return clbm.clbm_finish_sums(self.slab.ctx, clbm.REDUCE_TOTALS, s)
 
     def close(self):
         self.slab.close()
