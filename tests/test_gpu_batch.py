@@ -176,7 +176,7 @@ def test_config4_generator_cavities_against_oracle(precision):
     mixed Dirichlet / Neumann / Robin sides, heat sources, Ra up to 1e6; sides
     32..40 here so the oracle stays quick) in one batch, each against the FP64
     oracle after 300 steps, every field against its own largest value.  (These
-    small cavities at Ra ~ 1e5 have s_nu near 2 and amplify rounding
+    small cavities at Ra ~ 1e5 have s_nu of 1.7 and more and amplify rounding
     differences: after 1,000 steps the velocity differs by 1.3e-11 in FP64 and
     1.4e-5 in FP32, relative, beyond the per-format bounds.)"""
     ws = I.random_cavities(6, hmax=40)
