@@ -245,9 +245,9 @@ def run_reference(args):
 # GPU arm
 # ---------------------------------------------------------------------------
 def combine_ranks(elapsed_ms: float, nodes: int, steps: int, device=None):
-    """Whole-job throughput of independent replicas: the slowest rank's time
-    (max over ranks) bounds the job; every rank advanced `nodes` nodes for
-    `steps` steps.  Returns (max elapsed ms, MLUPS over all ranks)."""
+    """Whole-job throughput over the ranks (one y-slab each): the slowest
+    rank's time (max over ranks) bounds the job; every rank advanced `nodes`
+    nodes for `steps` steps.  Returns (max elapsed ms, MLUPS over all ranks)."""
     import torch
     import torch.distributed as dist
     world = dist.get_world_size() if dist.is_available() and dist.is_initialized() else 1

@@ -1,6 +1,6 @@
-"""Host logic of the multi-process benchmark path on CPU: two gloo ranks run
-independent replicas; the job time is the slowest rank's and the throughput
-counts every rank's nodes (weak scaling)."""
+"""Host logic of the multi-process benchmark path on CPU: two gloo ranks (one
+y-slab each); the job time is the slowest rank's and the throughput counts
+every rank's nodes (weak scaling)."""
 import os
 import socket
 
