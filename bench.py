@@ -38,6 +38,13 @@ sys.path.insert(0, ROOT)
 from paper_1801_04577_gb300 import inputs as I  # noqa: E402
 
 HBM_FALLBACK_GBS = 6800.0
+# FP64 storage and collision are bound by the FP64 pipe, not by HBM.  FP64 operations per
+# lattice update of step_fused_kernel<double>, counted with ncu on the 2048 x 1024
+# Rayleigh-Benard lattice (sm__sass_thread_inst_executed_op_{dfma,dadd,dmul}_pred_on: 170.1 M
+# DFMA, 160.6 M DADD, 88.2 M DMUL per launch of 2,097,152 nodes; an FMA counts two): 280.9.
+FP64_FLOP_PER_LU = 280.9
+# FP64 peak of the GB300: 152 SMs x 2 FP64 FMA per clock x 2 flops x 2.07 GHz
+FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07
 ELEM_BYTES = {"f64": 8, "f32": 4, "f16": 2, "bf16": 2}
 DTYPE = {"f64": "f64", "f32": "f32", "f16": "f16-storage/f32-compute", "bf16": "bf16-storage/f32-compute"}
 
@@ -428,11 +435,19 @@ def run_native(args):
                            parallelism={"dist": f"yslab{world} (one slab per GPU, NCCL halo exchange)",
                                         "group": f"yslab{args.slabs} on one GPU (device halo copies)",
                                         "single": "single"}[mode]),
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": traffic,
-                         "kernel": step_kernel_name(w),
-                         "peak_kind": peak_kind,
-                         "algorithmic_bytes_per_launch": bytes_lu * nodes},
+            "roofline": ({"bound": "alu", "achieved": FP64_FLOP_PER_LU * nodes / per_launch_s / 1e9,
+                          "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
+                          "frac": FP64_FLOP_PER_LU * nodes / per_launch_s / 1e9 / FP64_PEAK_GFLOPS,
+                          "traffic": traffic, "kernel": step_kernel_name(w),
+                          "peak_kind": "derived: 152 SMs x 2 FP64 FMA/clock x 2 x 2.07 GHz",
+                          "flop_per_lattice_update": FP64_FLOP_PER_LU,
+                          "hbm_frac": achieved / peak}
+                         if args.precision == "f64" else
+                         {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                          "frac": achieved / peak, "traffic": traffic,
+                          "kernel": step_kernel_name(w),
+                          "peak_kind": peak_kind,
+                          "algorithmic_bytes_per_launch": bytes_lu * nodes}),
             # slabs: one step launch per slab per step, plus (one process) one halo-copy launch
             "gpu_launches": step_launches(w, args.steps) if mode == "single" else args.steps * (
                 args.slabs + 1 if mode == "group" else 1),

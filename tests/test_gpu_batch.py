@@ -174,12 +174,14 @@ def test_batch_with_walls_off_the_link_midpoint():
 def test_config4_generator_cavities_against_oracle(precision):
     """Cavities of the 512-cavity generator (uneven sides, both orientations,
     mixed Dirichlet / Neumann / Robin sides, heat sources, Ra up to 1e6; sides
-    32..40 here so the oracle stays quick) in one batch, each against the FP64
-    oracle after 300 steps, every field against its own largest value.  (These
-    small cavities at Ra ~ 1e5 have s_nu of 1.7 and more and amplify rounding
-    differences: after 1,000 steps the velocity differs by 1.3e-11 in FP64 and
-    1.4e-5 in FP32, relative, beyond the per-format bounds.)"""
+    32..40 here so the oracle stays quick) in one batch, each started from
+    seeded random rho, u, T (so that every field is O(1e-2) from the first
+    step: from rest the velocity of these cavities is still far below U after a
+    few hundred steps) and compared with the FP64 oracle after 300 steps, every
+    field against its own largest value."""
     ws = I.random_cavities(6, hmax=40)
+    for k, w in enumerate(ws):
+        w.init = I.random_fields(w.params.nx, w.params.ny, seed=400 + k, amp=0.02)
     b = clbm.Batch(ws, precision, autotune=True)
     conv, _, steps = b.solve(0.0, 300, check_every=150)
     assert steps == 300 and (conv == -1).all()
