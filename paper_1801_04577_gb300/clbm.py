@@ -184,11 +184,26 @@ def clbm_set_boundaries(ctx, solid: Optional[np.ndarray], tbc: Sequence, side_tb
            "clbm_set_boundaries")
 
 
+def _host_f64(b):
+    """A host field for the library: a raw address (int) or a contiguous FP64
+    CPU tensor passes through as it is; anything else becomes a contiguous
+    FP64 numpy array."""
+    if b is None or isinstance(b, int):
+        return b
+    if hasattr(b, "data_ptr"):
+        if getattr(b, "is_cuda", False):
+            raise ValueError("device tensor passed as a host field (use on_device=True)")
+        if str(b.dtype) != "torch.float64" or not b.is_contiguous():
+            raise ValueError("host tensors must be contiguous float64")
+        return b
+    return np.ascontiguousarray(b, dtype=np.float64)
+
+
 def clbm_init_fields(ctx, rho=None, ux=None, uy=None, T=None, on_device: bool = False):
     L = load()
     bufs = [rho, ux, uy, T]
     if not on_device:
-        bufs = [None if b is None else np.ascontiguousarray(b, dtype=np.float64) for b in bufs]
+        bufs = [_host_f64(b) for b in bufs]
     _check(L.clbm_init_fields(ctx, *[_addr(b) for b in bufs], int(on_device)), ctx,
            "clbm_init_fields")
 

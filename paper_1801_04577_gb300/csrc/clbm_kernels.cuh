@@ -940,10 +940,11 @@ __global__ void init_kernel(const DevGeom g, const DevCoef cf, S* __restrict__ d
                             const double* __restrict__ uy, const double* __restrict__ T) {
   using R = typename Traits<S>::R;
   const Co<R> c = make_co<R>(cf);
-  const long long n = (long long)g.ny * g.pitch;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-       i += (long long)gridDim.x * blockDim.x) {
-    const int y = (int)(i / g.pitch), x = (int)(i - (long long)y * g.pitch);
+  // one thread per column of the padded rows (every stored row, ghost rows too)
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= g.pitch) return;
+  for (int y = (int)blockIdx.y; y < g.ny; y += (int)gridDim.y) {
+    const long long i = (long long)y * g.pitch + x;
     R d[9], h[5];
     bool active = x < g.nx && y >= g.ylo && y < g.yhi;  // own rows (ghost rows: zero until exchanged)
     if (g.flags) active = active && !(g.flags[i] & kFlagSolid);
@@ -1019,17 +1020,67 @@ __device__ __forceinline__ void node_macros_r(const Co<R>& c, bool vh, const S* 
   uy = (jy - R(0.5) * Fy) * inv;
 }
 
+// Sums of one node's stored deviations in the arithmetic R: the zeroth and
+// first moments of d*, the zeroth moment of h* and the viscous source slot.
+template <typename R>
+struct NodeSums {
+  R dr, jx, jy, s, qv;
+};
+
+template <typename R, typename S>
+__device__ __forceinline__ NodeSums<R> node_sums(const S* __restrict__ b, long long plane,
+                                                 long long i, bool vh) {
+  R f[9];
+  NodeSums<R> o;
+  o.s = R(0);
+#pragma unroll
+  for (int q = 0; q < 9; ++q) f[q] = (R)to_r(b[q * plane + i]);
+#pragma unroll
+  for (int q = 9; q < 14; ++q) o.s += (R)to_r(b[q * plane + i]);
+  o.qv = vh ? (R)to_r(b[14 * plane + i]) : R(0);
+  o.dr = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
+  o.jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
+  o.jy = (f[2] - f[4]) + (f[5] - f[7]) + (f[6] - f[8]);
+  return o;
+}
+
+// The reported fields of one fluid node.  FP64 storage: all in FP64.  Below
+// it the sums and the velocity take the collision's FP32 arithmetic (the
+// precision the state carries) and only the offsets rho0 and T0 are added in
+// FP64, so that the deviations of rho and T keep every bit the sums have.
+// Fy uses T - qv/2 - T0 = sum h* - Q/2 - qv, without the cancellation of T0.
+template <typename S>
+__device__ __forceinline__ void node_fields(const DevCoef& c, const Co<typename Traits<S>::R>& co,
+                                            const S* __restrict__ b, long long plane, long long i,
+                                            double& rho, double& ux, double& uy, double& T) {
+  using R = typename Traits<S>::R;
+  if constexpr (std::is_same<R, double>::value) {
+    node_macros(c, b, plane, i, rho, ux, uy, T);
+  } else {
+    const NodeSums<R> n = node_sums<R>(b, plane, i, c.vh != 0);
+    const R Fy = co.Fvy + co.rgb * (n.s - R(0.5) * co.Q - n.qv);
+    const R inv = R(1) / (co.rho0 + n.dr);
+    ux = (double)((n.jx - R(0.5) * co.Fvx) * inv);
+    uy = (double)((n.jy - R(0.5) * Fy) * inv);
+    rho = c.rho0 + (double)n.dr;
+    T = c.T0 + (double)(n.s - R(0.5) * (co.Q + n.qv));
+  }
+}
+
+// One thread per column x of the own rows; the rows are strided over gridDim.y.
 template <typename S>
 __global__ void moments_kernel(const DevGeom g, const DevCoef c, const S* __restrict__ b,
                                double* __restrict__ rho, double* __restrict__ ux,
                                double* __restrict__ uy, double* __restrict__ T) {
-  const long long n = (long long)(g.yhi - g.ylo) * g.nx;  // own rows
-  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
-       k += (long long)gridDim.x * blockDim.x) {
-    const int yl = (int)(k / g.nx), x = (int)(k - (long long)yl * g.nx);
-    const long long i = (long long)(yl + g.ylo) * g.pitch + x;
+  using R = typename Traits<S>::R;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= g.nx) return;
+  const Co<R> co = make_co<R>(c);
+  for (int y = g.ylo + (int)blockIdx.y; y < g.yhi; y += (int)gridDim.y) {
+    const long long i = (long long)y * g.pitch + x;
+    const long long k = (long long)(y - g.ylo) * g.nx + x;  // own-row index
     double r = 0, u = 0, v = 0, t = 0;
-    if (!g.flags || !(g.flags[i] & kFlagSolid)) node_macros(c, b, g.plane, i, r, u, v, t);
+    if (!g.flags || !(g.flags[i] & kFlagSolid)) node_fields<S>(c, co, b, g.plane, i, r, u, v, t);
     if (rho) rho[k] = r;
     if (ux) ux[k] = u;
     if (uy) uy[k] = v;
@@ -1065,27 +1116,107 @@ __device__ __forceinline__ void block_sum_store(double (&acc)[W], double* out) {
   }
 }
 
+// Squared one-step changes and squares of T, ux, uy at one fluid node, added
+// to a[0..5] (a[6] counts a non-finite field).  FP64 storage: the fields of
+// both states in FP64 and their differences.  Below it, in FP32 from the
+// differences of the stored values, which are exact where the state barely
+// moves (the differences of FP32 fields near rho0 and T0 would be rounded to
+// their ulp):
+//   dT = sum dh* - dqv/2,  du = (da - u(t-1) d(drho)) / rho(t),
+// a = j - F/2 with dFy = rgb (sum dh* - dqv) (a(t) = a(t-1) + da, rho(t) =
+// rho(t-1) + d(drho)).  Fields beyond ~1e19 overflow the FP32 squares and
+// count as unstable, as a non-finite field does.
+template <typename S, typename R>
+__device__ __forceinline__ void residual_terms(const DevCoef& c, const Co<R>& co,
+                                               const S* __restrict__ cur,
+                                               const S* __restrict__ prev, long long plane,
+                                               long long i, R (&a)[7]) {
+  if constexpr (std::is_same<R, double>::value) {
+    double r1, u1, v1, t1, r0, u0, v0, t0;
+    node_macros(c, cur, plane, i, r1, u1, v1, t1);
+    node_macros(c, prev, plane, i, r0, u0, v0, t0);
+    a[0] += (t1 - t0) * (t1 - t0);
+    a[1] += t1 * t1;
+    a[2] += (u1 - u0) * (u1 - u0);
+    a[3] += u1 * u1;
+    a[4] += (v1 - v0) * (v1 - v0);
+    a[5] += v1 * v1;
+    if (!isfinite(r1) || !isfinite(u1) || !isfinite(v1) || !isfinite(t1)) a[6] += 1.0;
+  } else {
+    const bool vh = c.vh != 0;
+    R f1[9], f0[9], df[9], s1 = R(0), s0 = R(0), ds = R(0);
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+      f1[q] = (R)to_r(cur[q * plane + i]);
+      f0[q] = (R)to_r(prev[q * plane + i]);
+      df[q] = f1[q] - f0[q];
+    }
+#pragma unroll
+    for (int q = 9; q < 14; ++q) {
+      const R h1 = (R)to_r(cur[q * plane + i]), h0 = (R)to_r(prev[q * plane + i]);
+      s1 += h1;
+      s0 += h0;
+      ds += h1 - h0;
+    }
+    const R q1 = vh ? (R)to_r(cur[14 * plane + i]) : R(0);
+    const R q0 = vh ? (R)to_r(prev[14 * plane + i]) : R(0);
+    auto zeroth = [](const R* f) {
+      return ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
+    };
+    auto first_x = [](const R* f) { return (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]); };
+    auto first_y = [](const R* f) { return (f[2] - f[4]) + (f[5] - f[7]) + (f[6] - f[8]); };
+    const R dq = q1 - q0;
+    const R t1 = co.T0 + (s1 - R(0.5) * (co.Q + q1));
+    const R dT = ds - R(0.5) * dq;
+    const R Fy1 = co.Fvy + co.rgb * (s1 - R(0.5) * co.Q - q1);
+    const R Fy0 = co.Fvy + co.rgb * (s0 - R(0.5) * co.Q - q0);
+    const R rho1 = co.rho0 + zeroth(f1), rho0 = co.rho0 + zeroth(f0), ddr = zeroth(df);
+    const R inv1 = R(1) / rho1, inv0 = R(1) / rho0;
+    const R u1 = (first_x(f1) - R(0.5) * co.Fvx) * inv1;
+    const R v1 = (first_y(f1) - R(0.5) * Fy1) * inv1;
+    const R u0 = (first_x(f0) - R(0.5) * co.Fvx) * inv0;
+    const R v0 = (first_y(f0) - R(0.5) * Fy0) * inv0;
+    const R dax = first_x(df), day = first_y(df) - R(0.5) * co.rgb * (ds - dq);
+    const R du = (dax - u0 * ddr) * inv1, dv = (day - v0 * ddr) * inv1;
+    a[0] += dT * dT;
+    a[1] += t1 * t1;
+    a[2] += du * du;
+    a[3] += u1 * u1;
+    a[4] += dv * dv;
+    a[5] += v1 * v1;
+    if (!isfinite(rho1) || !isfinite(u1) || !isfinite(v1) || !isfinite(t1)) a[6] += R(1);
+  }
+}
+
+// Work items are (own row, span of kRedThreads * kResV columns); a thread
+// sums its kResV nodes of an item in R and adds that to its FP64 sums.  The
+// items' partial sums depend on the row and columns alone, so slabs of one
+// lattice add the same numbers (in another order).
+constexpr int kResV = 8;
+
 template <typename S>
 __global__ void __launch_bounds__(kRedThreads)
     residual_kernel(const DevGeom g, const DevCoef c, const S* __restrict__ cur,
                     const S* __restrict__ prev, double* __restrict__ partials) {
+  using R = typename Traits<S>::R;
+  const Co<R> co = make_co<R>(c);
   double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-  const long long n = (long long)(g.yhi - g.ylo) * g.nx;  // own rows
-  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
-       k += (long long)gridDim.x * blockDim.x) {
-    const int yl = (int)(k / g.nx), x = (int)(k - (long long)yl * g.nx);
-    const long long i = (long long)(yl + g.ylo) * g.pitch + x;
-    if (g.flags && (g.flags[i] & kFlagSolid)) continue;
-    double r1, u1, v1, t1, r0, u0, v0, t0;
-    node_macros(c, cur, g.plane, i, r1, u1, v1, t1);
-    node_macros(c, prev, g.plane, i, r0, u0, v0, t0);
-    acc[0] += (t1 - t0) * (t1 - t0);
-    acc[1] += t1 * t1;
-    acc[2] += (u1 - u0) * (u1 - u0);
-    acc[3] += u1 * u1;
-    acc[4] += (v1 - v0) * (v1 - v0);
-    acc[5] += v1 * v1;
-    if (!isfinite(r1) || !isfinite(u1) || !isfinite(v1) || !isfinite(t1)) acc[6] += 1.0;
+  constexpr int span = kRedThreads * kResV;
+  const int xch = (g.nx + span - 1) / span;
+  const long long items = (long long)(g.yhi - g.ylo) * xch;
+  for (long long it = blockIdx.x; it < items; it += gridDim.x) {
+    const int yr = (int)(it / xch);
+    const int x0 = (int)(it - (long long)yr * xch) * span + (int)threadIdx.x;
+    const long long row = (long long)(yr + g.ylo) * g.pitch;
+    R a[7] = {0, 0, 0, 0, 0, 0, 0};
+#pragma unroll
+    for (int j = 0; j < kResV; ++j) {
+      const int x = x0 + j * kRedThreads;
+      if (x < g.nx && !(g.flags && (g.flags[row + x] & kFlagSolid)))
+        residual_terms<S, R>(c, co, cur, prev, g.plane, row + x, a);
+    }
+#pragma unroll
+    for (int q = 0; q < 7; ++q) acc[q] += (double)a[q];
   }
   block_sum_store<8>(acc, partials + 8 * blockIdx.x);
 }
@@ -1380,16 +1511,19 @@ struct LaunchImpl {
 
   static cudaError_t init(const DevGeom& g, const DevCoef& c, void* dst, const double* rho,
                           const double* ux, const double* uy, const double* T, cudaStream_t s) {
-    const long long n = (long long)g.ny * g.pitch;
-    init_kernel<S><<<blocks_for(n, 256), 256, 0, s>>>(g, c, static_cast<S*>(dst), rho, ux, uy, T);
+    if (g.ny <= 0 || g.pitch <= 0) return cudaSuccess;
+    const dim3 grid((g.pitch + 255) / 256, g.ny < 65535 ? g.ny : 65535);
+    init_kernel<S><<<grid, 256, 0, s>>>(g, c, static_cast<S*>(dst), rho, ux, uy, T);
     return cudaGetLastError();
   }
 
   static cudaError_t moments(const DevGeom& g, const DevCoef& c, const void* buf, double* rho,
                              double* ux, double* uy, double* T, cudaStream_t s) {
-    const long long n = (long long)(g.yhi - g.ylo) * g.nx;
-    moments_kernel<S><<<blocks_for(n, 256), 256, 0, s>>>(g, c, static_cast<const S*>(buf), rho,
-                                                          ux, uy, T);
+    const int rows = g.yhi - g.ylo;
+    if (rows <= 0 || g.nx <= 0) return cudaSuccess;
+    const int threads = g.nx >= 256 ? 256 : (g.nx + 31) / 32 * 32;
+    const dim3 grid((g.nx + threads - 1) / threads, rows < 65535 ? rows : 65535);
+    moments_kernel<S><<<grid, threads, 0, s>>>(g, c, static_cast<const S*>(buf), rho, ux, uy, T);
     return cudaGetLastError();
   }
 

@@ -69,3 +69,33 @@ def test_null_arguments():
     assert L.clbm_totals(None, out) == clbm.CLBM_EINVAL
     assert L.clbm_residual(None, out) == clbm.CLBM_EINVAL
     assert L.clbm_nusselt(None, 0, 1.0, 1.0, out) == clbm.CLBM_EINVAL
+
+
+def test_host_field_addresses_pass_through_unchanged(monkeypatch):
+    """clbm_init_fields with host fields: a raw address (int) and a contiguous
+    FP64 CPU tensor reach the library as the caller's own address; only
+    array-likes are converted.  (A raw address once became the address of a
+    one-element array, and the library copied nx * ny doubles from it.)"""
+    import numpy as np
+    import torch
+
+    seen = []
+
+    class Fake:
+        def clbm_init_fields(self, ctx, *args):
+            seen.append(args)
+            return clbm.CLBM_OK
+
+    monkeypatch.setattr(clbm, "load", lambda: Fake())
+    t = torch.arange(12, dtype=torch.float64)
+    a = np.arange(12, dtype=np.float32)
+    clbm.clbm_init_fields(None, None, 0x7F00_0000_1000, t, a, on_device=False)
+    rho, ux, uy, T, dev = seen[-1]
+    assert rho is None and ux == 0x7F00_0000_1000 and uy == t.data_ptr() and dev == 0
+    assert T not in (None, a.ctypes.data)  # converted to a new FP64 array
+    with pytest.raises(ValueError):
+        clbm.clbm_init_fields(None, t.float(), on_device=False)
+    with pytest.raises(ValueError):
+        clbm.clbm_init_fields(None, t[::2], on_device=False)
+    clbm.clbm_init_fields(None, 1234, 5678, on_device=True)
+    assert seen[-1][:2] == (1234, 5678) and seen[-1][4] == 1
