@@ -418,8 +418,9 @@ def run_native(args):
         el2 = float(el2_t.item())
         e2e = {"value": world * nodes * args.steps / el2 / 1e6, "unit": "MLUPS",
                "h2d_bytes_per_step": 8 * n / args.steps, "d2h_bytes_per_step": 3 * 8 * n / args.steps,
-               "note": f"per run: one clbm_init_fields from pinned host T ({8 * n} B), "
-                       f"{args.steps} steps, one clbm_moments of ux, uy, T to pinned host "
+               "note": f"per run: one clbm_init_fields from pinned host T ({8 * n} B, read over "
+                       f"the host link by the initialisation kernel), {args.steps} steps, one "
+                       f"clbm_moments of ux, uy, T written by the kernel to pinned host "
                        f"({24 * n} B); bytes reported per lattice step; after one untimed run "
                        f"of the same sequence with the warm-up step count"}
 

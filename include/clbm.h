@@ -163,7 +163,11 @@ clbm_status clbm_set_wall_velocity(clbm_ctx* ctx, int32_t side, double ux, doubl
  * Eq. 9 and Eq. 19 at the given fields, i.e. f(t=0) = f^eq(rho, u),
  * g(t=0) = g^eq(T, u), and reset the step counter.  Each pointer is an FP64
  * [ny][nx] array or NULL for the rest value (rho0, 0, 0, T0).  on_device
- * selects device (1) or host (0) pointers. */
+ * selects device (1) or host (0) pointers.  Host arrays: exactly nx * ny
+ * doubles are read from each; page-locked memory mapped into the device's
+ * address space (cudaHostAlloc, cudaHostRegister) is read by the kernel in
+ * place, pageable memory is copied through a device scratch allocated on first
+ * use.  With host pointers the call synchronises before it returns. */
 clbm_status clbm_init_fields(clbm_ctx* ctx, const double* rho, const double* ux, const double* uy,
                              const double* T, int32_t on_device);
 
@@ -175,7 +179,9 @@ clbm_status clbm_step(clbm_ctx* ctx, int64_t nsteps);
 /* Macroscopic fields at the current time: rho = sum f (Eq. 12),
  * u = (sum f e + F/2)/rho (Eq. 12), T = sum g + Q/2 (Eq. 25), as FP64
  * [ny][nx] arrays; solid nodes report 0.  Any pointer may be NULL.
- * on_device selects device (1) or host (0) outputs; host outputs synchronise. */
+ * on_device selects device (1) or host (0) outputs; host outputs synchronise.
+ * Each host output receives exactly nx * ny doubles: the kernel writes mapped
+ * page-locked memory in place and pageable memory through the device scratch. */
 clbm_status clbm_moments(clbm_ctx* ctx, double* rho, double* ux, double* uy, double* T,
                          int32_t on_device);
 

@@ -596,6 +596,19 @@ static clbm_status ensure_fields_scratch(clbm_ctx* c) {
   return CLBM_OK;
 }
 
+// The device's view of a host buffer that kernels may read and write in place:
+// page-locked host memory mapped into the device's address space (on a
+// Grace-Blackwell node the GPU reaches it coherently over NVLink-C2C, at the
+// rate of the copy engines).  nullptr for pageable memory.
+static void* mapped_view(const void* p) {
+  cudaPointerAttributes a;
+  if (!p || cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 clbm_status clbm_init_fields(clbm_ctx* c, const double* rho, const double* ux, const double* uy,
                              const double* T, int32_t on_device) {
   if (!c) return CLBM_EINVAL;
@@ -605,10 +618,14 @@ clbm_status clbm_init_fields(clbm_ctx* c, const double* rho, const double* ux, c
   if (on_device) {
     for (int k = 0; k < 4; ++k) dev[k] = src[k];
   } else if (rho || ux || uy || T) {
-    clbm_status st = ensure_fields_scratch(c);
-    if (st != CLBM_OK) return st;
+    // mapped page-locked fields are read by the kernel itself, so the
+    // transfer overlaps the initialisation; pageable ones go through the scratch
     for (int k = 0; k < 4; ++k) {
       if (!src[k]) continue;
+      dev[k] = static_cast<const double*>(mapped_view(src[k]));
+      if (dev[k]) continue;
+      clbm_status st = ensure_fields_scratch(c);
+      if (st != CLBM_OK) return st;
       double* d = c->d_fields + k * n;
       CLBM_CUDA(c, cudaMemcpyAsync(d, src[k], n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
       dev[k] = d;
@@ -852,15 +869,23 @@ clbm_status clbm_moments(clbm_ctx* c, double* rho, double* ux, double* uy, doubl
     CLBM_CUDA(c, c->L->moments(make_geom(c), make_coef(c), c->buf[c->cur], rho, ux, uy, T, c->stream));
     return CLBM_OK;
   }
-  clbm_status st = ensure_fields_scratch(c);
-  if (st != CLBM_OK) return st;
+  // the kernel writes mapped page-locked outputs in place; pageable ones are
+  // written to the scratch and copied
   double* d[4];
+  bool staged[4] = {false, false, false, false};
   double* h[4] = {rho, ux, uy, T};
-  for (int k = 0; k < 4; ++k) d[k] = h[k] ? c->d_fields + k * n : nullptr;
+  for (int k = 0; k < 4; ++k) {
+    d[k] = h[k] ? static_cast<double*>(mapped_view(h[k])) : nullptr;
+    if (!h[k] || d[k]) continue;
+    clbm_status st = ensure_fields_scratch(c);
+    if (st != CLBM_OK) return st;
+    d[k] = c->d_fields + k * n;
+    staged[k] = true;
+  }
   CLBM_CUDA(c, c->L->moments(make_geom(c), make_coef(c), c->buf[c->cur], d[0], d[1], d[2], d[3],
                              c->stream));
   for (int k = 0; k < 4; ++k)
-    if (h[k]) CLBM_CUDA(c, cudaMemcpyAsync(h[k], d[k], n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    if (staged[k]) CLBM_CUDA(c, cudaMemcpyAsync(h[k], d[k], n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   CLBM_CUDA(c, cudaStreamSynchronize(c->stream));
   return CLBM_OK;
 }
