@@ -715,6 +715,16 @@ struct clbm_net {
   int sms = 152;  // multiprocessors of the device (one wave = 5 CTAs per SM)
   Plan plan{};
   std::string err;
+  // A pass captured as a CUDA graph on its first call with a given set of
+  // buffers and batch size, and replayed while they stay the same (the buffer
+  // contents may change between calls).
+  struct Captured {
+    cudaGraphExec_t exec = nullptr;
+    const void *a = nullptr, *b = nullptr, *c = nullptr;
+    int N = 0;
+  };
+  Captured grad_pass, fwd_pass;
+  double* h_loss = nullptr;  // page-locked copy of the loss partials and mask sums
 };
 
 namespace {
@@ -1000,6 +1010,44 @@ cudaError_t backward(clbm_net* net, const Plan& P, int N) {
   return cudaGetLastError();
 }
 
+// Enqueue a pass (`body` launches it on net->stream) as a replayed graph: the
+// first call with a new key (the pass's buffers and batch size) captures it,
+// later calls with the same key launch the instantiated graph, one launch for
+// the whole pass.  A stream that cannot be captured (the legacy default
+// stream) runs the pass directly.
+template <class F>
+cudaError_t run_captured(clbm_net* net, clbm_net::Captured& g, const void* a, const void* b, const void* c,
+                         int N, F body) {
+  if (g.exec && g.a == a && g.b == b && g.c == c && g.N == N) return cudaGraphLaunch(g.exec, net->stream);
+  if (g.exec) {
+    cudaGraphExecDestroy(g.exec);
+    g.exec = nullptr;
+  }
+  if (cudaStreamBeginCapture(net->stream, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+    cudaGetLastError();
+    return body();
+  }
+  const cudaError_t eb = body();
+  cudaGraph_t graph = nullptr;
+  const cudaError_t ec = cudaStreamEndCapture(net->stream, &graph);
+  if (eb || ec) {
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    return eb ? eb : ec;
+  }
+  const cudaError_t ei = cudaGraphInstantiate(&g.exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ei) {
+    g.exec = nullptr;
+    return ei;
+  }
+  g.a = a;
+  g.b = b;
+  g.c = c;
+  g.N = N;
+  return cudaGraphLaunch(g.exec, net->stream);
+}
+
 clbm_status nfail(clbm_net* n, clbm_status s, const std::string& m) {
   if (n) n->err = m;
   return s;
@@ -1044,6 +1092,9 @@ clbm_status clbm_net_destroy(clbm_net* n) {
   for (float* a : n->gact) cudaFree(a);
   cudaFree(n->part);
   cudaFree(n->loss_part);
+  if (n->grad_pass.exec) cudaGraphExecDestroy(n->grad_pass.exec);
+  if (n->fwd_pass.exec) cudaGraphExecDestroy(n->fwd_pass.exec);
+  if (n->h_loss) cudaFreeHost(n->h_loss);
   if (n->tflag) cudaFreeHost(n->tflag);
   cudaFree(n->packed);
   cudaFree(n->d_pack);
@@ -1176,7 +1227,8 @@ clbm_status clbm_net_create(const clbm_net_config* cfg, uint64_t seed, void* str
   *n->tflag = 0;
   if (cudaHostGetDevicePointer(&n->d_tflag, n->tflag, 0) != cudaSuccess) return bail(CLBM_ECUDA);
   if (cudaMalloc(&n->part, cap * sizeof(float)) ||
-      cudaMalloc(&n->loss_part, (size_t)c.max_batch * (kLossChunks + 1) * sizeof(double)))
+      cudaMalloc(&n->loss_part, (size_t)c.max_batch * (kLossChunks + 1) * sizeof(double)) ||
+      cudaHostAlloc(&n->h_loss, (size_t)c.max_batch * (kLossChunks + 1) * sizeof(double), cudaHostAllocDefault))
     return bail(CLBM_ENOMEM);
   if (cudaStreamSynchronize(n->stream) != cudaSuccess) return bail(CLBM_ECUDA);
   *out = n;
@@ -1216,9 +1268,12 @@ clbm_status clbm_net_forward(clbm_net* n, const float* x, int32_t N, float* y) {
   const Plan& P = n->plan;
   const long long in_e = (long long)N * n->cfg.in_ch * n->cfg.grid * n->cfg.grid;
   const long long out_e = (long long)N * n->cfg.out_ch * n->cfg.grid * n->cfg.grid;
-  cudaError_t e = cudaMemcpyAsync(n->act[P.in], x, in_e * sizeof(float), cudaMemcpyDeviceToDevice, n->stream);
-  if (!e) e = forward(n, P, N);
-  if (!e) e = cudaMemcpyAsync(y, n->act[P.out], out_e * sizeof(float), cudaMemcpyDeviceToDevice, n->stream);
+  const cudaError_t e = run_captured(n, n->fwd_pass, x, y, nullptr, N, [&]() {
+    cudaError_t e = cudaMemcpyAsync(n->act[P.in], x, in_e * sizeof(float), cudaMemcpyDeviceToDevice, n->stream);
+    if (!e) e = forward(n, P, N);
+    if (!e) e = cudaMemcpyAsync(y, n->act[P.out], out_e * sizeof(float), cudaMemcpyDeviceToDevice, n->stream);
+    return e;
+  });
   return cuda_status(n, e, "forward");
 }
 
@@ -1228,28 +1283,31 @@ clbm_status clbm_net_gradients(clbm_net* n, const float* x, const float* target,
   const Plan& P = n->plan;
   const int G = n->cfg.grid, C = n->cfg.out_ch;
   const long long in_e = (long long)N * n->cfg.in_ch * G * G;
-  cudaError_t e = cudaMemcpyAsync(n->act[P.in], x, in_e * sizeof(float), cudaMemcpyDeviceToDevice, n->stream);
-  if (!e) e = forward(n, P, N);
   // loss normalisation (sum of mask weights times channels) on the device, so
   // that the backward pass follows the forward pass without a host round trip
   double* mpart = n->loss_part + (size_t)n->cfg.max_batch * kLossChunks;
-  if (!e && mask) {
-    mask_sum_kernel<<<N, GT, 0, n->stream>>>(mask, G * G, mpart);
-    e = cudaGetLastError();
-  }
-  if (!e) {
-    loss_kernel<<<dim3(N, kLossChunks), GT, 0, n->stream>>>(n->act[P.out], target, mask, mpart, N, C, G * G,
-                                                            n->gact[P.out], n->loss_part);
-    e = cudaGetLastError();
-  }
-  if (!e) e = backward(n, P, N);
-  std::vector<double> lp((size_t)N * kLossChunks + N);
-  if (!e)
-    e = cudaMemcpyAsync(lp.data(), n->loss_part, (size_t)N * kLossChunks * sizeof(double), cudaMemcpyDeviceToHost,
-                        n->stream);
-  if (!e && mask)
-    e = cudaMemcpyAsync(lp.data() + (size_t)N * kLossChunks, mpart, (size_t)N * sizeof(double),
-                        cudaMemcpyDeviceToHost, n->stream);
+  const double* lp = n->h_loss;
+  cudaError_t e = run_captured(n, n->grad_pass, x, target, mask, N, [&]() {
+    cudaError_t e = cudaMemcpyAsync(n->act[P.in], x, in_e * sizeof(float), cudaMemcpyDeviceToDevice, n->stream);
+    if (!e) e = forward(n, P, N);
+    if (!e && mask) {
+      mask_sum_kernel<<<N, GT, 0, n->stream>>>(mask, G * G, mpart);
+      e = cudaGetLastError();
+    }
+    if (!e) {
+      loss_kernel<<<dim3(N, kLossChunks), GT, 0, n->stream>>>(n->act[P.out], target, mask, mpart, N, C, G * G,
+                                                              n->gact[P.out], n->loss_part);
+      e = cudaGetLastError();
+    }
+    if (!e) e = backward(n, P, N);
+    if (!e)
+      e = cudaMemcpyAsync(n->h_loss, n->loss_part, (size_t)N * kLossChunks * sizeof(double),
+                          cudaMemcpyDeviceToHost, n->stream);
+    if (!e && mask)
+      e = cudaMemcpyAsync(n->h_loss + (size_t)N * kLossChunks, mpart, (size_t)N * sizeof(double),
+                          cudaMemcpyDeviceToHost, n->stream);
+    return e;
+  });
   if (!e) e = cudaStreamSynchronize(n->stream);
   if (e) return cuda_status(n, e, "gradients");
   if (timed_out(n)) return nfail(n, CLBM_ETIMEOUT, kTimeoutMsg);

@@ -149,6 +149,40 @@ def test_adam_training_reduces_loss_on_fixed_batch():
     net.close()
 
 
+@pytest.mark.parametrize("math", ["tensor", "fp32"])
+def test_replayed_passes_follow_the_buffer_contents(math):
+    """The forward and gradient passes are captured on their first call with a
+    set of buffers and replayed afterwards: a replay reads the buffers' current
+    contents (new inputs in the same tensors), and gives what a first call on
+    those contents gives (a fresh network with the same weights), bit for bit."""
+    G, N = 16, 3
+    x, t, m = _batch(G, 5, 3, N, seed=91)
+    x2, t2, _ = _batch(G, 5, 3, N, seed=92)
+    xd, td, md = (torch.from_numpy(a).cuda() for a in (x, t, m))
+    net = Net(G, 5, 3, 8, 3, N, seed=7, math=math)
+    l1, g1 = net.gradients(xd, td, md)
+    l1b, g1b = net.gradients(xd, td, md)  # replay, same contents
+    assert l1b == l1 and np.array_equal(g1b, g1)
+    xd.copy_(torch.from_numpy(x2))
+    td.copy_(torch.from_numpy(t2))
+    torch.cuda.synchronize()  # the network runs on its own stream
+    l2, g2 = net.gradients(xd, td, md)  # replay, new contents
+    y = torch.empty((N, 3, G, G), device="cuda")
+    net.forward(xd, y)
+    net.forward(xd, y)
+    torch.cuda.synchronize()
+    fresh = Net(G, 5, 3, 8, 3, N, seed=7, math=math)
+    x2d, t2d = torch.from_numpy(x2).cuda(), torch.from_numpy(t2).cuda()
+    l2r, g2r = fresh.gradients(x2d, t2d, md)
+    y2 = torch.empty_like(y)
+    fresh.forward(x2d, y2)
+    torch.cuda.synchronize()
+    assert l2 == l2r and np.array_equal(g2, g2r) and l2 != l1
+    assert torch.equal(y, y2)
+    net.close()
+    fresh.close()
+
+
 def test_warm_start_reaches_steady_state_in_fewer_steps():
     """Train on solver-generated steady states of 32^2 obstacle cavities, then
     solve held-out problems from rest and from the network's prediction: the
