@@ -559,6 +559,49 @@ def conv_flops_per_train_step(G, cin, cout, base, levels, batch):
     return total
 
 
+def conv_bytes_per_train_step(G, cin, cout, base, levels, batch, elem_bytes=4):
+    """Algorithmic DRAM bytes of the convolution passes of one training step:
+    each pass reads its input activations and writes its output once (FP32
+    activations); the weight gradients read the layer input and the output
+    gradient.  The weights themselves are small beside the activations."""
+    from paper_1801_04577_gb300.net import layer_shapes
+    shapes = layer_shapes(G, cin, cout, base, levels)
+    res = []
+    for l in range(levels - 1):
+        res += [G >> l, G >> l]
+    res += [G >> (levels - 1)] * 2
+    for l in range(levels - 2, -1, -1):
+        res += [G >> l, G >> l]
+    res.append(G)
+    total = 0.0
+    for li, ((ci, co, k), h) in enumerate(zip(shapes, res)):
+        total += (ci + co) * batch * h * h * elem_bytes * (2 if li == 0 else 3)
+    return total
+
+
+def conv_roofline_ms(G, cin, cout, base, levels, batch, tflops, gbs):
+    """Lower bound on a training step's convolution time: every pass at the
+    larger of its tensor-core time (flops at the BF16 peak) and its DRAM time
+    (its activation bytes at the copy bandwidth).  At these widths (24-192
+    channels) most passes are memory-bound: 2 x 9 ci x co flops per (ci + co)
+    x 4 bytes is below the machine balance of the tensor cores."""
+    from paper_1801_04577_gb300.net import layer_shapes
+    shapes = layer_shapes(G, cin, cout, base, levels)
+    res = []
+    for l in range(levels - 1):
+        res += [G >> l, G >> l]
+    res += [G >> (levels - 1)] * 2
+    for l in range(levels - 2, -1, -1):
+        res += [G >> l, G >> l]
+    res.append(G)
+    t = 0.0
+    for li, ((ci, co, k), h) in enumerate(zip(shapes, res)):
+        f = 2.0 * batch * h * h * co * ci * k * k
+        b = (ci + co) * batch * h * h * 4
+        t += max(f / (tflops * 1e12), b / (gbs * 1e9)) * (2 if li == 0 else 3)
+    return t * 1e3
+
+
 def run_unet(args):
     """Training steps of the warm-start U-Net on the tensor cores (default: 64^2
     grid, widths 24..192, 1.1 M parameters, batch 32; --net-grid 128 gives the
@@ -602,12 +645,15 @@ def run_unet(args):
     f1.record(stream)
     torch.cuda.synchronize()
     flops = conv_flops_per_train_step(G, cin, cout, base, levels, B)
+    nbytes = conv_bytes_per_train_step(G, cin, cout, base, levels, B)
     achieved = flops / (ms * 1e-3) / 1e12
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
             peak, kind = float(json.load(fh)["bf16_tflops"]), "measured bf16 burst"
     except Exception:
         peak, kind = 1900.0, "fallback bf16 burst"
+    hbm, hbm_kind = measured_peak()
+    roof_ms = conv_roofline_ms(G, cin, cout, base, levels, B, peak, hbm)
     line = {"metric": "train_samples_per_s", "value": B * 1000.0 / ms, "unit": "samples/s",
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -617,10 +663,15 @@ def run_unet(args):
                        "parameters": net.nparam, "forward_ms": f0.elapsed_time(f1) / 20,
                        "conv_gflop_per_step": flops / 1e9, "loss_last": loss,
                        "l2": f"activations of one batch (~{0.3 * (G / 64) ** 2:.1f} GB) larger than L2 in the first level"},
-            "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak, "traffic": None,
-                         "kernel": "tc::gemm_kernel (all convolution GEMMs of a training step)",
-                         "peak_kind": kind},
+            # most convolution passes are memory-bound at these widths: the bound is
+            # the activations' DRAM bytes; the tensor-core rate is reported beside it
+            "roofline": {"bound": "hbm", "achieved": nbytes / (ms * 1e-3) / 1e9, "peak": hbm,
+                         "unit": "GB/s", "frac": nbytes / (ms * 1e-3) / 1e9 / hbm, "traffic": None,
+                         "kernel": "tc::gemm_kernel (all convolution passes of a training step)",
+                         "peak_kind": hbm_kind, "algorithmic_bytes_per_step": nbytes,
+                         "roofline_ms": roof_ms, "roofline_time_frac": roof_ms / ms,
+                         "tensor_tflops": achieved, "tensor_peak": peak, "tensor_frac": achieved / peak,
+                         "tensor_peak_kind": kind},
             "gpu_launches": None}
     if clocks is not None:
         line["clocks"] = clocks
