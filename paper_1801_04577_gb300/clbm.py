@@ -178,8 +178,8 @@ def clbm_set_boundaries(ctx, solid: Optional[np.ndarray], tbc: Sequence, side_tb
         larr[k] = clbm_link(int(link_node[k]), int(link_dir[k]), float(link_ne[k]), int(link_tbc[k]), 0,
                             0.5 if link_q is None else float(link_q[k]))
     sol = None
-    if solid is not None:
-        sol = np.ascontiguousarray(solid, dtype=np.uint8)
+    if solid is not None:  # a raw host address passes through; arrays become uint8
+        sol = solid if isinstance(solid, int) else np.ascontiguousarray(solid, dtype=np.uint8)
     _check(L.clbm_set_boundaries(ctx, _addr(sol), tarr, n_tbc, sides, larr, n_links), ctx,
            "clbm_set_boundaries")
 
@@ -308,7 +308,9 @@ def clbm_reduce_sums(ctx, what: int, which: int = 0) -> np.ndarray:
 
 
 def clbm_finish_sums(ctx, what: int, sums, length: float = 0.0, dT: float = 1.0) -> np.ndarray:
-    h = np.ascontiguousarray(sums, np.float64)
+    h = np.ascontiguousarray(sums, np.float64).ravel()
+    if h.size < 8:
+        raise ValueError("clbm_finish_sums takes the eight sums of clbm_reduce_sums")
     out = np.zeros(4, np.float64)
     _check(load().clbm_finish_sums(ctx, int(what), h.ctypes.data_as(C.POINTER(C.c_double)), float(length),
                                    float(dT), out.ctypes.data_as(C.POINTER(C.c_double))), None,
@@ -338,11 +340,19 @@ def clbm_last_error(ctx) -> str:
 # --------------------------------------------------------------------------
 # Convenience wrapper around one context
 # --------------------------------------------------------------------------
+def _check_solid_shape(geom, params):
+    """The library copies ny * nx mask bytes: a mask of any other shape is refused here."""
+    solid = None if geom is None else geom.solid
+    if solid is not None and np.shape(solid) != (params.ny, params.nx):
+        raise ValueError(f"solid mask of shape {np.shape(solid)} for a {params.ny} x {params.nx} lattice")
+
+
 class Solver:
     """One lattice on the GPU, described by ``inputs.Params`` / ``inputs.Geometry``."""
 
     def __init__(self, params, geom=None, precision="f32", stream: Optional[int] = None, init=None,
                  rounding: int = 0):
+        _check_solid_shape(geom, params)
         self.params = params
         self.nx, self.ny = params.nx, params.ny
         self.precision = precision
@@ -409,6 +419,7 @@ class Slab(Solver):
         self.nx, self.ny = params.nx, rows
         self.y0, self.rows = y0, rows
         self.precision = precision
+        _check_solid_shape(geom, params)
         self.ctx = clbm_create_slab(make_params(params, precision, rounding), y0, rows, stream)
         if geom is not None:
             clbm_set_boundaries(self.ctx, geom.solid, geom.tbc, geom.side_tbc, geom.link_node,
@@ -497,6 +508,7 @@ class Batch:
             if any(ux or uy for ux, uy in (getattr(g, "side_u", None) or ())):
                 raise ValueError(f"{w.name}: batched lattices have walls at rest")
             shape = (p.ny, p.nx)
+            _check_solid_shape(g, p)
             tbc = (clbm_tbc * max(len(g.tbc), 1))(*[clbm_tbc(*map(float, t)) for t in g.tbc])
             nl = g.n_links
             links = (clbm_link * max(nl, 1))()

@@ -715,9 +715,9 @@ struct clbm_net {
   int sms = 152;  // multiprocessors of the device (one wave = 5 CTAs per SM)
   Plan plan{};
   std::string err;
-  // A pass captured as a CUDA graph on its first call with a given set of
-  // buffers and batch size, and replayed while they stay the same (the buffer
-  // contents may change between calls).
+  // A pass captured as a CUDA graph on its first call with a given key (batch
+  // size, mask or none) and replayed while the key stays the same; the pass
+  // reads and writes the network's own buffers only.
   struct Captured {
     cudaGraphExec_t exec = nullptr;
     const void *a = nullptr, *b = nullptr, *c = nullptr;
@@ -725,6 +725,7 @@ struct clbm_net {
   };
   Captured grad_pass, fwd_pass;
   double* h_loss = nullptr;  // page-locked copy of the loss partials and mask sums
+  float *tgt = nullptr, *msk = nullptr;  // the caller's target and mask, copied in before a pass
 };
 
 namespace {
@@ -1011,10 +1012,10 @@ cudaError_t backward(clbm_net* net, const Plan& P, int N) {
 }
 
 // Enqueue a pass (`body` launches it on net->stream) as a replayed graph: the
-// first call with a new key (the pass's buffers and batch size) captures it,
-// later calls with the same key launch the instantiated graph, one launch for
-// the whole pass.  A stream that cannot be captured (the legacy default
-// stream) runs the pass directly.
+// first call with a new key (batch size, mask or none) captures it, later
+// calls with the same key launch the instantiated graph, one launch for the
+// whole pass.  A stream that cannot be captured (the legacy default stream)
+// runs the pass directly.
 template <class F>
 cudaError_t run_captured(clbm_net* net, clbm_net::Captured& g, const void* a, const void* b, const void* c,
                          int N, F body) {
@@ -1095,6 +1096,8 @@ clbm_status clbm_net_destroy(clbm_net* n) {
   if (n->grad_pass.exec) cudaGraphExecDestroy(n->grad_pass.exec);
   if (n->fwd_pass.exec) cudaGraphExecDestroy(n->fwd_pass.exec);
   if (n->h_loss) cudaFreeHost(n->h_loss);
+  cudaFree(n->tgt);
+  cudaFree(n->msk);
   if (n->tflag) cudaFreeHost(n->tflag);
   cudaFree(n->packed);
   cudaFree(n->d_pack);
@@ -1228,7 +1231,9 @@ clbm_status clbm_net_create(const clbm_net_config* cfg, uint64_t seed, void* str
   if (cudaHostGetDevicePointer(&n->d_tflag, n->tflag, 0) != cudaSuccess) return bail(CLBM_ECUDA);
   if (cudaMalloc(&n->part, cap * sizeof(float)) ||
       cudaMalloc(&n->loss_part, (size_t)c.max_batch * (kLossChunks + 1) * sizeof(double)) ||
-      cudaHostAlloc(&n->h_loss, (size_t)c.max_batch * (kLossChunks + 1) * sizeof(double), cudaHostAllocDefault))
+      cudaHostAlloc(&n->h_loss, (size_t)c.max_batch * (kLossChunks + 1) * sizeof(double), cudaHostAllocDefault) ||
+      cudaMalloc(&n->tgt, (size_t)c.max_batch * c.out_ch * c.grid * c.grid * sizeof(float)) ||
+      cudaMalloc(&n->msk, (size_t)c.max_batch * c.grid * c.grid * sizeof(float)))
     return bail(CLBM_ENOMEM);
   if (cudaStreamSynchronize(n->stream) != cudaSuccess) return bail(CLBM_ECUDA);
   *out = n;
@@ -1268,12 +1273,11 @@ clbm_status clbm_net_forward(clbm_net* n, const float* x, int32_t N, float* y) {
   const Plan& P = n->plan;
   const long long in_e = (long long)N * n->cfg.in_ch * n->cfg.grid * n->cfg.grid;
   const long long out_e = (long long)N * n->cfg.out_ch * n->cfg.grid * n->cfg.grid;
-  const cudaError_t e = run_captured(n, n->fwd_pass, x, y, nullptr, N, [&]() {
-    cudaError_t e = cudaMemcpyAsync(n->act[P.in], x, in_e * sizeof(float), cudaMemcpyDeviceToDevice, n->stream);
-    if (!e) e = forward(n, P, N);
-    if (!e) e = cudaMemcpyAsync(y, n->act[P.out], out_e * sizeof(float), cudaMemcpyDeviceToDevice, n->stream);
-    return e;
-  });
+  // the caller's buffers are copied in and out around the replayed pass, whose
+  // graph then depends on the batch size alone
+  cudaError_t e = cudaMemcpyAsync(n->act[P.in], x, in_e * sizeof(float), cudaMemcpyDeviceToDevice, n->stream);
+  if (!e) e = run_captured(n, n->fwd_pass, nullptr, nullptr, nullptr, N, [&]() { return forward(n, P, N); });
+  if (!e) e = cudaMemcpyAsync(y, n->act[P.out], out_e * sizeof(float), cudaMemcpyDeviceToDevice, n->stream);
   return cuda_status(n, e, "forward");
 }
 
@@ -1287,15 +1291,23 @@ clbm_status clbm_net_gradients(clbm_net* n, const float* x, const float* target,
   // that the backward pass follows the forward pass without a host round trip
   double* mpart = n->loss_part + (size_t)n->cfg.max_batch * kLossChunks;
   const double* lp = n->h_loss;
-  cudaError_t e = run_captured(n, n->grad_pass, x, target, mask, N, [&]() {
-    cudaError_t e = cudaMemcpyAsync(n->act[P.in], x, in_e * sizeof(float), cudaMemcpyDeviceToDevice, n->stream);
-    if (!e) e = forward(n, P, N);
-    if (!e && mask) {
-      mask_sum_kernel<<<N, GT, 0, n->stream>>>(mask, G * G, mpart);
+  // inputs copied in first: the replayed pass depends on the batch size and on
+  // whether there is a mask, not on the caller's buffers
+  const float* msk = mask ? n->msk : nullptr;
+  cudaError_t e = cudaMemcpyAsync(n->act[P.in], x, in_e * sizeof(float), cudaMemcpyDeviceToDevice, n->stream);
+  if (!e)
+    e = cudaMemcpyAsync(n->tgt, target, (size_t)N * C * G * G * sizeof(float), cudaMemcpyDeviceToDevice,
+                        n->stream);
+  if (!e && mask)
+    e = cudaMemcpyAsync(n->msk, mask, (size_t)N * G * G * sizeof(float), cudaMemcpyDeviceToDevice, n->stream);
+  if (!e) e = run_captured(n, n->grad_pass, msk, nullptr, nullptr, N, [&]() {
+    cudaError_t e = forward(n, P, N);
+    if (!e && msk) {
+      mask_sum_kernel<<<N, GT, 0, n->stream>>>(msk, G * G, mpart);
       e = cudaGetLastError();
     }
     if (!e) {
-      loss_kernel<<<dim3(N, kLossChunks), GT, 0, n->stream>>>(n->act[P.out], target, mask, mpart, N, C, G * G,
+      loss_kernel<<<dim3(N, kLossChunks), GT, 0, n->stream>>>(n->act[P.out], n->tgt, msk, mpart, N, C, G * G,
                                                               n->gact[P.out], n->loss_part);
       e = cudaGetLastError();
     }

@@ -70,6 +70,18 @@ def _ptr(t) -> Optional[int]:
     return int(t)
 
 
+def _check_dev(t, shape, name):
+    """A device tensor the library reads or writes in full: refuse a wrong shape,
+    dtype or layout here rather than let a kernel run past its end.  Raw
+    addresses (int) are the caller's responsibility."""
+    if t is None or isinstance(t, int):
+        return
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name}: shape {tuple(t.shape)}, expected {tuple(shape)}")
+    if str(getattr(t, "dtype", "")) != "torch.float32" or not t.is_contiguous() or not t.is_cuda:
+        raise ValueError(f"{name}: a contiguous float32 CUDA tensor is expected")
+
+
 class Net:
     """U-Net surrogate; see clbm_net_create for the architecture."""
 
@@ -101,14 +113,25 @@ class Net:
         return out
 
     def set_params(self, p: np.ndarray):
-        p = np.ascontiguousarray(p, np.float32)
+        p = np.ascontiguousarray(p, np.float32).ravel()
+        if p.size != self.nparam:
+            raise ValueError(f"{p.size} parameters for a network of {self.nparam}")
         _check(load().clbm_net_set_params(self.h, p.ctypes.data, 0), self.h, "set_params")
+
+    def _check_batch(self, x, target=None, mask=None, y=None):
+        G, N = self.cfg.grid, int(x.shape[0])
+        _check_dev(x, (N, self.cfg.in_ch, G, G), "x")
+        _check_dev(target, (N, self.cfg.out_ch, G, G), "target")
+        _check_dev(y, (N, self.cfg.out_ch, G, G), "y")
+        _check_dev(mask, (N, G, G), "mask")
 
     def forward(self, x, y):
         """x, y: torch CUDA float32 tensors [N, C, G, G] (async on the net's stream)."""
+        self._check_batch(x, y=y)
         _check(load().clbm_net_forward(self.h, _ptr(x), int(x.shape[0]), _ptr(y)), self.h, "forward")
 
     def gradients(self, x, target, mask=None):
+        self._check_batch(x, target, mask)
         g = np.empty(self.nparam, np.float32)
         loss = C.c_double()
         _check(load().clbm_net_gradients(self.h, _ptr(x), _ptr(target), _ptr(mask), int(x.shape[0]),
@@ -116,6 +139,7 @@ class Net:
         return loss.value, g
 
     def train_step(self, x, target, mask, lr: float) -> float:
+        self._check_batch(x, target, mask)
         loss = C.c_double()
         _check(load().clbm_net_train_step(self.h, _ptr(x), _ptr(target), _ptr(mask), int(x.shape[0]),
                                           float(lr), C.byref(loss)), self.h, "train_step")

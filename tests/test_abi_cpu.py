@@ -99,3 +99,19 @@ def test_host_field_addresses_pass_through_unchanged(monkeypatch):
         clbm.clbm_init_fields(None, t[::2], on_device=False)
     clbm.clbm_init_fields(None, 1234, 5678, on_device=True)
     assert seen[-1][:2] == (1234, 5678) and seen[-1][4] == 1
+
+
+def test_mask_and_sums_of_the_wrong_size_are_refused_before_the_library():
+    """The library copies ny * nx mask bytes and eight sums: shorter inputs are
+    refused by the binding (no GPU needed: the checks come first)."""
+    import numpy as np
+    w = I.natural_convection_cavity(12, 1e4)
+    w.geom.solid = np.zeros((11, 12), np.uint8)
+    with pytest.raises(ValueError):
+        clbm.Solver(w.params, w.geom)
+    with pytest.raises(ValueError):
+        clbm.Slab(w.params, 0, 6, w.geom)
+    with pytest.raises(ValueError):
+        clbm.Batch([w])
+    with pytest.raises(ValueError):
+        clbm.clbm_finish_sums(None, 0, np.zeros(7))

@@ -152,9 +152,10 @@ def test_adam_training_reduces_loss_on_fixed_batch():
 @pytest.mark.parametrize("math", ["tensor", "fp32"])
 def test_replayed_passes_follow_the_buffer_contents(math):
     """The forward and gradient passes are captured on their first call with a
-    set of buffers and replayed afterwards: a replay reads the buffers' current
-    contents (new inputs in the same tensors), and gives what a first call on
-    those contents gives (a fresh network with the same weights), bit for bit."""
+    batch size and replayed afterwards, the caller's tensors copied in and out
+    around them: a replay follows new contents of the same tensors and other
+    tensors alike, and gives what a first call gives (a fresh network with the
+    same weights), bit for bit."""
     G, N = 16, 3
     x, t, m = _batch(G, 5, 3, N, seed=91)
     x2, t2, _ = _batch(G, 5, 3, N, seed=92)
@@ -179,6 +180,11 @@ def test_replayed_passes_follow_the_buffer_contents(math):
     torch.cuda.synchronize()
     assert l2 == l2r and np.array_equal(g2, g2r) and l2 != l1
     assert torch.equal(y, y2)
+    l3, g3 = net.gradients(x2d, t2d, md)  # replay from other tensors
+    assert l3 == l2r and np.array_equal(g3, g2r)
+    l4, g4 = net.gradients(x2d, t2d)  # no mask: its own capture
+    l4r, g4r = fresh.gradients(x2d, t2d)
+    assert l4 == l4r and np.array_equal(g4, g4r) and l4 != l3
     net.close()
     fresh.close()
 
