@@ -469,6 +469,11 @@ clbm_status clbm_batch_damp_period2(clbm_batch* b);
 /* Number of time steps taken since the last initialisation. */
 clbm_status clbm_time(const clbm_ctx* ctx, int64_t* t_out);
 
+/* Shape of the fields clbm_init_fields reads and clbm_moments writes: nx
+ * columns by the context's own rows (ny, or a slab's rows), i.e. each field
+ * array holds nx * rows doubles.  Errors: CLBM_EINVAL for a NULL argument. */
+clbm_status clbm_field_shape(const clbm_ctx* ctx, int64_t* nx_out, int64_t* rows_out);
+
 /* Free every device and host resource of the context (NULL is allowed). */
 clbm_status clbm_destroy(clbm_ctx* ctx);
 

@@ -54,7 +54,7 @@ EXPORTS = ["clbm_create", "clbm_set_boundaries", "clbm_init_fields", "clbm_step"
            "clbm_damp_period2", "clbm_batch_damp_period2",
            "clbm_set_wall_velocity", "clbm_create_slab", "clbm_halo_bytes", "clbm_halo_pack", "clbm_halo_unpack", "clbm_halo_copy",
            "clbm_slabs_exchange", "clbm_slabs_step", "clbm_reduce_sums", "clbm_finish_sums",
-           "clbm_batch_last_error", "clbm_time", "clbm_destroy", "clbm_last_error",
+           "clbm_batch_last_error", "clbm_time", "clbm_field_shape", "clbm_destroy", "clbm_last_error",
            "clbm_status_string"]
 
 _lib = None
@@ -90,6 +90,7 @@ def load(path: Optional[str] = None):
     L.clbm_totals.argtypes = [vp, dp]
     L.clbm_residual_fields_noalloc.argtypes = [vp] * 7 + [C.c_int64, vp, dp]
     L.clbm_time.argtypes = [vp, C.POINTER(C.c_int64)]
+    L.clbm_field_shape.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
     L.clbm_destroy.argtypes = [vp]
     L.clbm_last_error.argtypes = [vp]
     L.clbm_last_error.restype = C.c_char_p
@@ -199,11 +200,39 @@ def _host_f64(b):
     return np.ascontiguousarray(b, dtype=np.float64)
 
 
+def clbm_field_shape(ctx):
+    """(nx, rows) of the fields of a context: each field holds nx * rows doubles."""
+    nx, rows = C.c_int64(), C.c_int64()
+    _check(load().clbm_field_shape(ctx, C.byref(nx), C.byref(rows)), ctx, "clbm_field_shape")
+    return nx.value, rows.value
+
+
+def _check_fields(ctx, bufs, on_device, what):
+    """Every field array (not a raw address) must hold nx * rows FP64 values on
+    the side `on_device` names: the library reads or writes all of them."""
+    if all(b is None or isinstance(b, int) for b in bufs):
+        return
+    nx, rows = clbm_field_shape(ctx)
+    for b in bufs:
+        if b is None or isinstance(b, int):
+            continue
+        if hasattr(b, "data_ptr"):
+            ok = (b.numel() == nx * rows and str(b.dtype) == "torch.float64" and b.is_contiguous()
+                  and bool(b.is_cuda) == bool(on_device))
+        else:
+            ok = (not on_device and isinstance(b, np.ndarray) and b.size == nx * rows
+                  and b.dtype == np.float64 and b.flags["C_CONTIGUOUS"])
+        if not ok:
+            raise ValueError(f"{what}: each field must be {rows} x {nx} contiguous float64 "
+                             f"{'device' if on_device else 'host'} values")
+
+
 def clbm_init_fields(ctx, rho=None, ux=None, uy=None, T=None, on_device: bool = False):
     L = load()
     bufs = [rho, ux, uy, T]
     if not on_device:
         bufs = [_host_f64(b) for b in bufs]
+    _check_fields(ctx, bufs, on_device, "clbm_init_fields")
     _check(L.clbm_init_fields(ctx, *[_addr(b) for b in bufs], int(on_device)), ctx,
            "clbm_init_fields")
 
@@ -213,6 +242,7 @@ def clbm_step(ctx, nsteps: int):
 
 
 def clbm_moments(ctx, rho=None, ux=None, uy=None, T=None, on_device: bool = False):
+    _check_fields(ctx, (rho, ux, uy, T), on_device, "clbm_moments")
     _check(load().clbm_moments(ctx, *[_addr(b) for b in (rho, ux, uy, T)], int(on_device)), ctx,
            "clbm_moments")
 
@@ -271,11 +301,24 @@ def clbm_halo_bytes(ctx) -> int:
     return out.value
 
 
+def _check_halo_buffer(ctx, buf, what):
+    """A device tensor given as a halo buffer must hold clbm_halo_bytes bytes
+    (the library writes or reads all of them); raw addresses pass unchecked."""
+    if isinstance(buf, int) or not hasattr(buf, "data_ptr"):
+        return
+    have = buf.numel() * buf.element_size()
+    need = clbm_halo_bytes(ctx)
+    if have < need or not buf.is_contiguous() or not buf.is_cuda:
+        raise ValueError(f"{what}: a contiguous CUDA buffer of {need} bytes is needed, got {have}")
+
+
 def clbm_halo_pack(ctx, side: int, dst):
+    _check_halo_buffer(ctx, dst, "clbm_halo_pack")
     _check(load().clbm_halo_pack(ctx, int(side), _addr(dst)), ctx, "clbm_halo_pack")
 
 
 def clbm_halo_unpack(ctx, side: int, src):
+    _check_halo_buffer(ctx, src, "clbm_halo_unpack")
     _check(load().clbm_halo_unpack(ctx, int(side), _addr(src)), ctx, "clbm_halo_unpack")
 
 

@@ -861,6 +861,13 @@ clbm_status clbm_time(const clbm_ctx* c, int64_t* t_out) {
   return CLBM_OK;
 }
 
+clbm_status clbm_field_shape(const clbm_ctx* c, int64_t* nx_out, int64_t* rows_out) {
+  if (!c || !nx_out || !rows_out) return CLBM_EINVAL;
+  *nx_out = c->p.nx;
+  *rows_out = c->yhi - c->ylo;
+  return CLBM_OK;
+}
+
 clbm_status clbm_moments(clbm_ctx* c, double* rho, double* ux, double* uy, double* T,
                          int32_t on_device) {
   if (!c) return CLBM_EINVAL;

@@ -86,6 +86,10 @@ def test_host_field_addresses_pass_through_unchanged(monkeypatch):
             seen.append(args)
             return clbm.CLBM_OK
 
+        def clbm_field_shape(self, ctx, nx, rows):
+            nx._obj.value, rows._obj.value = 4, 3
+            return clbm.CLBM_OK
+
     monkeypatch.setattr(clbm, "load", lambda: Fake())
     t = torch.arange(12, dtype=torch.float64)
     a = np.arange(12, dtype=np.float32)
@@ -97,6 +101,10 @@ def test_host_field_addresses_pass_through_unchanged(monkeypatch):
         clbm.clbm_init_fields(None, t.float(), on_device=False)
     with pytest.raises(ValueError):
         clbm.clbm_init_fields(None, t[::2], on_device=False)
+    with pytest.raises(ValueError):  # 13 values for a 3 x 4 field
+        clbm.clbm_init_fields(None, np.zeros(13), on_device=False)
+    with pytest.raises(ValueError):  # a host tensor where device fields are asked for
+        clbm.clbm_init_fields(None, t, on_device=True)
     clbm.clbm_init_fields(None, 1234, 5678, on_device=True)
     assert seen[-1][:2] == (1234, 5678) and seen[-1][4] == 1
 
