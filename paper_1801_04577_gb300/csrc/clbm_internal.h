@@ -63,16 +63,69 @@ struct CoefF32 {
   float pad;
 };
 
+// The collision's rates combined with the exact power-of-two scalings of the
+// form it relaxes in (moments of order one and two halved per direction, so
+// that the back-transformation needs no halving of its own): computed once on
+// the host in FP64, and rounded once for the FP32 kernels.
+template <typename T>
+struct CollideK {
+  T hFx, hr0;                // Fvx / 2, rho0 / 2
+  T sb4, snu4, snur4;        // (1 - s_b) / 4, (1 - s_nu) / 4, s_nu rho0 / 4
+  T s3m4, s3r4, hs3q;        // (1 - s3) / 4, s3 rho0 / 4, (1 - s3 / 2) / 12
+  T s4m4, s4r4, s4n;         // (1 - s4) / 4, s4 rho0 / 4, s4 / 36
+  T l1m2, l1T2, l2m2, l2T2;  // (1 - l1) / 2, l1 T0 / 2, (1 - l2) / 2, l2 T0 / 2
+  T srcq2, srct2;            // (1 - l2 / 2) cT2 / 2, l2 cT2 / 2
+};
+
 struct DevCoef {
   double s_nu, s_b, s3, s4, l0, l1, l2;
   double rho0, T0, gbeta, Fvx, Fvy, Q, cT2;
   int vh;  // 1: viscous dissipation source (stored as a 15th plane, Q_v at each node)
   int pad;
-  CoefF32 f;  // filled by fill_f32
+  CoefF32 f;            // filled by fill_f32
+  CollideK<double> kd;  // filled by fill_f32
+  CollideK<float> kf;
 };
 
-// FP32 copies of a DevCoef's constants (each computed in FP64, then rounded).
+// FP32 copies of a DevCoef's constants (each computed in FP64, then rounded),
+// and the combined collision constants in both precisions.
 inline void fill_f32(DevCoef& k) {
+  CollideK<double>& d = k.kd;
+  d.hFx = 0.5 * k.Fvx;
+  d.hr0 = 0.5 * k.rho0;
+  d.sb4 = 0.25 * (1.0 - k.s_b);
+  d.snu4 = 0.25 * (1.0 - k.s_nu);
+  d.snur4 = 0.25 * k.s_nu * k.rho0;
+  d.s3m4 = 0.25 * (1.0 - k.s3);
+  d.s3r4 = 0.25 * k.s3 * k.rho0;
+  d.hs3q = (1.0 - 0.5 * k.s3) / 12.0;
+  d.s4m4 = 0.25 * (1.0 - k.s4);
+  d.s4r4 = 0.25 * k.s4 * k.rho0;
+  d.s4n = k.s4 / 36.0;
+  d.l1m2 = 0.5 * (1.0 - k.l1);
+  d.l1T2 = 0.5 * k.l1 * k.T0;
+  d.l2m2 = 0.5 * (1.0 - k.l2);
+  d.l2T2 = 0.5 * k.l2 * k.T0;
+  d.srcq2 = 0.5 * (1.0 - 0.5 * k.l2) * k.cT2;
+  d.srct2 = 0.5 * k.l2 * k.cT2;
+  CollideK<float>& e = k.kf;
+  e.hFx = (float)d.hFx;
+  e.hr0 = (float)d.hr0;
+  e.sb4 = (float)d.sb4;
+  e.snu4 = (float)d.snu4;
+  e.snur4 = (float)d.snur4;
+  e.s3m4 = (float)d.s3m4;
+  e.s3r4 = (float)d.s3r4;
+  e.hs3q = (float)d.hs3q;
+  e.s4m4 = (float)d.s4m4;
+  e.s4r4 = (float)d.s4r4;
+  e.s4n = (float)d.s4n;
+  e.l1m2 = (float)d.l1m2;
+  e.l1T2 = (float)d.l1T2;
+  e.l2m2 = (float)d.l2m2;
+  e.l2T2 = (float)d.l2T2;
+  e.srcq2 = (float)d.srcq2;
+  e.srct2 = (float)d.srct2;
   CoefF32& o = k.f;
   o.rho0 = (float)k.rho0;
   o.T0 = (float)k.T0;

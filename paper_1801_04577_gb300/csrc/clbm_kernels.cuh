@@ -231,12 +231,14 @@ struct Co {
   R rgb;   // rho0 * g beta
   R Fvx, Fvy, Q, hQ, cT2;
   R vhc;   // viscous source: Q_v = vhc (k~11^2 + (k~20 - k~02)^2 / 4) / rho^2
+  CollideK<R> k;  // rates combined with the scalings of the relaxed form
 };
 
 template <typename R>
 __host__ __device__ __forceinline__ Co<R> make_co(const DevCoef& c) {
   Co<R> o;
   if constexpr (std::is_same<R, float>::value) {  // rounded on the host
+    o.k = c.kf;
     const CoefF32& f = c.f;
     o.rho0 = f.rho0;
     o.T0 = f.T0;
@@ -254,6 +256,7 @@ __host__ __device__ __forceinline__ Co<R> make_co(const DevCoef& c) {
     o.cT2 = f.cT2;
     o.vhc = f.vhc;
   } else {
+    o.k = c.kd;
     o.rho0 = (R)c.rho0;
     o.T0 = (R)c.T0;
     o.s_nu = (R)c.s_nu;
@@ -298,6 +301,19 @@ __host__ __device__ __forceinline__ void inv1(R c0, R c1, R c2, R u, R& am, R& a
   ap = R(0.5) * (r2 + r1);
   am = R(0.5) * (r2 - r1);
 }
+// inv1 from halved first- and second-order inputs, c1h = c1 / 2 and c2h =
+// c2 / 2, with u2 = 2u, hu = u / 2, hu2 = u^2 / 2: h1 = r1 / 2 and h2 = r2 / 2
+// come out directly, so the two halvings of inv1 are not needed.  Scaling by
+// a power of two is exact, so the result is inv1's to rounding.
+template <typename R>
+__host__ __device__ __forceinline__ void inv1h(R c0, R c1h, R c2h, R u2, R hu, R hu2, R& am, R& a0,
+                                               R& ap) {
+  const R h1 = c1h + hu * c0;
+  const R h2 = c2h + u2 * c1h + hu2 * c0;
+  a0 = c0 - R(2) * h2;
+  ap = h2 + h1;
+  am = h2 - h1;
+}
 
 // ---------------------------------------------------------------------------
 // Collision of one node, on deviations.  In: pre-collision deviations d, h.
@@ -306,7 +322,39 @@ __host__ __device__ __forceinline__ void inv1(R c0, R c1, R c2, R u, R& am, R& a
 // VH: add the viscous dissipation source Q_v (Sec. 3.2), read from the
 // pre-collision non-equilibrium central moments; it is returned in qv.  The
 // Boussinesq force uses T without Q_v/2 (Q_v needs u, which needs the force).
-template <typename R, bool VH = false>
+// The combined constants: from the host (HK), or formed here from the rates
+// (the FP32-storage kernels, which are memory-bound, run about 1.4 % faster
+// with the latter as compiled; the 16-bit and FP64 ones, bound by issue or by
+// the FP64 pipe, with the former).
+template <typename R, bool HK>
+__host__ __device__ __forceinline__ CollideK<R> collide_k(const Co<R>& c) {
+  if constexpr (HK) {
+    return c.k;
+  } else {
+    const R q4 = R(0.25), h = R(0.5), third = R(1.0 / 3.0);
+    CollideK<R> k;
+    k.hFx = h * c.Fvx;
+    k.hr0 = h * c.rho0;
+    k.sb4 = (R(1) - c.s_b) * q4;
+    k.snu4 = (R(1) - c.s_nu) * q4;
+    k.snur4 = c.s_nu * c.rho0 * q4;
+    k.s3m4 = (R(1) - c.s3) * q4;
+    k.s3r4 = c.s3 * c.rho0 * q4;
+    k.hs3q = (R(1) - h * c.s3) * third * q4;
+    k.s4m4 = (R(1) - c.s4) * q4;
+    k.s4r4 = c.s4 * c.rho0 * q4;
+    k.s4n = c.s4 * R(1.0 / 36.0);
+    k.l1m2 = (R(1) - c.l1) * h;
+    k.l1T2 = c.l1 * c.T0 * h;
+    k.l2m2 = (R(1) - c.l2) * h;
+    k.l2T2 = c.l2 * c.T0 * h;
+    k.srcq2 = (R(1) - h * c.l2) * c.cT2 * h;
+    k.srct2 = c.l2 * c.cT2 * h;
+    return k;
+  }
+}
+
+template <typename R, bool VH = false, bool HK = true>
 __host__ __device__ __forceinline__ void collide(const Co<R>& c, R (&d)[9], R (&h)[5], R& qv) {
   const R third = R(1.0 / 3.0);
   // Eq. 25 (T - T0 = sum h + Q/2) and Eq. 2
@@ -330,8 +378,9 @@ __host__ __device__ __forceinline__ void collide(const Co<R>& c, R (&d)[9], R (&
 #ifdef __CUDA_ARCH__
   if constexpr (std::is_same<R, float>::value) inv_rho = __fdividef(1.0f, rho);
 #endif
-  const R ux = (jx + R(0.5) * Fx) * inv_rho;
-  const R uy = (jy + R(0.5) * Fy) * inv_rho;
+  const R hFx = R(0.5) * Fx, hFy = R(0.5) * Fy;
+  const R ux = (jx + hFx) * inv_rho;
+  const R uy = (jy + hFy) * inv_rho;
 
   // central moments of the deviations: x-pass per velocity row, then y-pass
   R xm1, xm2, xz1, xz2, xp1, xp2;
@@ -345,24 +394,27 @@ __host__ __device__ __forceinline__ void collide(const Co<R>& c, R (&d)[9], R (&
   fwd1(xm2, xz2, xp2, uy, b20, b21, b22);
 
   // Eq. 7-10, minus the rest-state moments rho0 kappa_m(ux) kappa_n(uy),
-  // kappa = (1, -u, 1/3 + u^2)
+  // kappa = (1, -u, 1/3 + u^2).  Each post-collision moment D_mn is formed
+  // scaled by 2^-[m > 0] 2^-[n > 0] (H_mn; exact scalings folded into the
+  // rates), the form the back-transformation inv1h takes on both passes.
   const R ux2 = ux * ux, uy2 = uy * uy;
   const R r0 = c.rho0;
-  const R D00 = b00;
-  const R D10 = b10 + Fx;
-  const R D01 = b01 + Fy;
-  const R a20 = r0 * ux2 + b20 - third * drho;
-  const R a02 = r0 * uy2 + b02 - third * drho;
-  const R sum = (R(1) - c.s_b) * (a20 + a02);
-  const R dif = (R(1) - c.s_nu) * (a20 - a02);
-  const R D20 = third * drho - r0 * ux2 + R(0.5) * (sum + dif);
-  const R D02 = third * drho - r0 * uy2 + R(0.5) * (sum - dif);
-  const R D11 = (R(1) - c.s_nu) * b11 - c.s_nu * r0 * ux * uy;
-  const R hs3 = (R(1) - R(0.5) * c.s3) * third;
-  const R D21 = (R(1) - c.s3) * b21 + c.s3 * r0 * (third + ux2) * uy + hs3 * Fy;
-  const R D12 = (R(1) - c.s3) * b12 + c.s3 * r0 * ux * (third + uy2) + hs3 * Fx;
-  const R D22 = (R(1) - c.s4) * b22 - c.s4 * r0 * (third * (ux2 + uy2) + ux2 * uy2) +
-                c.s4 * R(1.0 / 9.0) * drho;
+  const CollideK<R> k = collide_k<R, HK>(c);
+  const R H00 = b00;
+  const R H10 = R(0.5) * b10 + k.hFx;  // D10 / 2, D10 = b10 + Fx
+  const R H01 = R(0.5) * b01 + hFy;    // D01 / 2, D01 = b01 + Fy
+  const R tdr = third * drho;
+  const R a20 = r0 * ux2 + b20 - tdr;
+  const R a02 = r0 * uy2 + b02 - tdr;
+  const R sum = k.sb4 * (a20 + a02);   // (1 - s_b) / 4 (a20 + a02)
+  const R dif = k.snu4 * (a20 - a02);  // (1 - s_nu) / 4 (a20 - a02)
+  const R htdr = R(0.5) * tdr;
+  const R H20 = htdr - k.hr0 * ux2 + (sum + dif);  // D20 / 2
+  const R H02 = htdr - k.hr0 * uy2 + (sum - dif);  // D02 / 2
+  const R H11 = k.snu4 * b11 - k.snur4 * (ux * uy);  // D11 / 4
+  const R H21 = k.s3m4 * b21 + k.s3r4 * ((third + ux2) * uy) + k.hs3q * Fy;  // D21 / 4
+  const R H12 = k.s3m4 * b12 + k.s3r4 * (ux * (third + uy2)) + k.hs3q * Fx;  // D12 / 4
+  const R H22 = k.s4m4 * b22 - k.s4r4 * (third * (ux2 + uy2) + ux2 * uy2) + k.s4n * drho;  // D22 / 4
   R Qt = c.Q;
   qv = R(0);
   if constexpr (VH) {
@@ -372,14 +424,18 @@ __host__ __device__ __forceinline__ void collide(const Co<R>& c, R (&d)[9], R (&
     Qt = c.Q + qv;
   }
 
-  // back-transformation: y-pass inverse per x-order, then x-pass inverse per row
+  // back-transformation: y-pass inverse per x-order (rows m = 1, 2 come out
+  // halved, as the x-pass wants them), then x-pass inverse per row
+  const R ux2x = ux + ux, uy2x = uy + uy;
+  const R hux = R(0.5) * ux, huy = R(0.5) * uy;
+  const R hux2 = hux * ux, huy2 = huy * uy;
   R ym0, yz0, yp0, ym1, yz1, yp1, ym2, yz2, yp2;
-  inv1(D00, D01, D02, uy, ym0, yz0, yp0);
-  inv1(D10, D11, D12, uy, ym1, yz1, yp1);
-  inv1(D20, D21, D22, uy, ym2, yz2, yp2);
-  inv1(ym0, ym1, ym2, ux, d[7], d[4], d[8]);
-  inv1(yz0, yz1, yz2, ux, d[3], d[0], d[1]);
-  inv1(yp0, yp1, yp2, ux, d[6], d[2], d[5]);
+  inv1h(H00, H01, H02, uy2x, huy, huy2, ym0, yz0, yp0);
+  inv1h(H10, H11, H12, uy2x, huy, huy2, ym1, yz1, yp1);
+  inv1h(H20, H21, H22, uy2x, huy, huy2, ym2, yz2, yp2);
+  inv1h(ym0, ym1, ym2, ux2x, hux, hux2, d[7], d[4], d[8]);
+  inv1h(yz0, yz1, yz2, ux2x, hux, hux2, d[3], d[0], d[1]);
+  inv1h(yp0, yp1, yp2, ux2x, hux, hux2, d[6], d[2], d[5]);
 
   // thermal (Eq. 15-20, 23-24) on deviations from w^T T0; kappa^T = (1, -u, cT2 + u^2)
   const R k10 = h[1] - h[3], k01 = h[2] - h[4];
@@ -389,30 +445,37 @@ __host__ __device__ __forceinline__ void collide(const Co<R>& c, R (&d)[9], R (&
   const R t02 = k02 - (uy + uy) * k01 + uy2 * sh;
   const R T0 = c.T0;
   const R dTt = VH ? sh + R(0.5) * Qt : dT;  // Eq. 25 with the total source
+  // post-collision thermal moments, first and second order halved (G = E / 2)
+  // so that the back-transformation needs no halving of its own
   const R E00 = sh + Qt;
-  const R E10 = (R(1) - c.l1) * t10 + c.l1 * T0 * ux;
-  const R E01 = (R(1) - c.l1) * t01 + c.l1 * T0 * uy;
-  const R src2 = (R(1) - R(0.5) * c.l2) * Qt * c.cT2 + c.l2 * c.cT2 * dTt;
-  const R E20 = (R(1) - c.l2) * t20 - c.l2 * T0 * ux2 + src2;
-  const R E02 = (R(1) - c.l2) * t02 - c.l2 * T0 * uy2 + src2;
-  const R q10 = E10 + ux * E00, q01 = E01 + uy * E00;
-  const R q20 = E20 + (ux + ux) * E10 + ux2 * E00;
-  const R q02 = E02 + (uy + uy) * E01 + uy2 * E00;
-  h[0] = E00 - q20 - q02;
-  h[1] = R(0.5) * (q20 + q10);
-  h[3] = R(0.5) * (q20 - q10);
-  h[2] = R(0.5) * (q02 + q01);
-  h[4] = R(0.5) * (q02 - q01);
+  const R G10 = k.l1m2 * t10 + k.l1T2 * ux;
+  const R G01 = k.l1m2 * t01 + k.l1T2 * uy;
+  const R src2h = k.srcq2 * Qt + k.srct2 * dTt;
+  const R G20 = k.l2m2 * t20 - k.l2T2 * ux2 + src2h;
+  const R G02 = k.l2m2 * t02 - k.l2T2 * uy2 + src2h;
+  const R q10 = G10 + hux * E00, q01 = G01 + huy * E00;  // halves of the raw moments
+  const R q20 = G20 + ux2x * G10 + hux2 * E00;
+  const R q02 = G02 + uy2x * G01 + huy2 * E00;
+  h[0] = E00 - R(2) * (q20 + q02);
+  h[1] = q20 + q10;
+  h[3] = q20 - q10;
+  h[2] = q02 + q01;
+  h[4] = q02 - q01;
 }
 
-template <typename R>
+template <typename R, bool HK = true>
 __host__ __device__ __forceinline__ void collide_any(const Co<R>& c, bool vh, R (&d)[9], R (&h)[5],
                                                      R& qv) {
   if (vh)
-    collide<R, true>(c, d, h, qv);
+    collide<R, true, HK>(c, d, h, qv);
   else
-    collide<R, false>(c, d, h, qv);
+    collide<R, false, HK>(c, d, h, qv);
 }
+
+// Which constants the kernels of storage type S take (the same in every
+// kernel of one storage type, so that they all compute the same numbers).
+template <typename S>
+constexpr bool kHostK = !std::is_same<S, float>::value;
 
 // Pre-collision equilibrium deviations (central moments Eq. 9 and Eq. 19 minus
 // the rest-state moments) at (rho, u, T).
@@ -743,7 +806,7 @@ __device__ __forceinline__ void step_tile(const DevGeom& g, const Co<typename Tr
     for (int q = 0; q < 9; ++q) d[q] = v[q][k];
 #pragma unroll
     for (int q = 0; q < 5; ++q) h[q] = v[9 + q][k];
-    collide<R, VH>(c, d, h, qv[k]);
+    collide<R, VH, kHostK<S>>(c, d, h, qv[k]);
 #pragma unroll
     for (int q = 0; q < 9; ++q) v[q][k] = d[q];
 #pragma unroll
@@ -845,7 +908,7 @@ __device__ __forceinline__ void step_node(const DevGeom& g, const Co<typename Tr
   fixup<S, MASK>(g, c, src, x, y, fl, d, h);
   R qv;
   const bool vh = c.vhc != R(0);
-  collide_any(c, vh, d, h, qv);
+  collide_any<R, kHostK<S>>(c, vh, d, h, qv);
   if (vh) dst[14 * plane + i] = from_r<S, R>(qv);
   // global node index of the group of four (the pitch is a multiple of 4)
   const uint32_t key = sr_key(seed, i + (long long)g.yoff * g.pitch - (x & 3));
@@ -956,7 +1019,7 @@ __global__ void init_kernel(const DevGeom g, const DevCoef cf, S* __restrict__ d
       const R t = T ? (R)T[k] : c.T0;
       equilibrium(c, r, u, w, t, d, h);
       R qv;
-      collide_any(c, cf.vh != 0, d, h, qv);
+      collide_any<R, kHostK<S>>(c, cf.vh != 0, d, h, qv);
       if (cf.vh) dst[14 * g.plane + i] = from_r<S, R>(qv);
     } else {
       if (cf.vh) dst[14 * g.plane + i] = from_r<S, R>(R(0));
