@@ -69,10 +69,11 @@ struct CoefF32 {
 // the host in FP64, and rounded once for the FP32 kernels.
 template <typename T>
 struct CollideK {
-  T hFx, hr0;                // Fvx / 2, rho0 / 2
-  T sb4, snu4, snur4;        // (1 - s_b) / 4, (1 - s_nu) / 4, s_nu rho0 / 4
+  T hFx;                     // Fvx / 2
+  T al, be;                  // -(s_b + s_nu) / 4, (s_nu - s_b) / 4 (the k~20, k~02 block)
+  T snu4, snur4;             // (1 - s_nu) / 4, s_nu rho0 / 4
   T s3m4, s3r4, hs3q;        // (1 - s3) / 4, s3 rho0 / 4, (1 - s3 / 2) / 12
-  T s4m4, s4r4, s4n;         // (1 - s4) / 4, s4 rho0 / 4, s4 / 36
+  T s4m4, s4r4, s4n, s4r9;   // (1 - s4) / 4, s4 rho0 / 4, s4 / 36, s4 rho0 / 36
   T l1m2, l1T2, l2m2, l2T2;  // (1 - l1) / 2, l1 T0 / 2, (1 - l2) / 2, l2 T0 / 2
   T srcq2, srct2;            // (1 - l2 / 2) cT2 / 2, l2 cT2 / 2
 };
@@ -92,8 +93,8 @@ struct DevCoef {
 inline void fill_f32(DevCoef& k) {
   CollideK<double>& d = k.kd;
   d.hFx = 0.5 * k.Fvx;
-  d.hr0 = 0.5 * k.rho0;
-  d.sb4 = 0.25 * (1.0 - k.s_b);
+  d.al = -0.25 * (k.s_b + k.s_nu);
+  d.be = 0.25 * (k.s_nu - k.s_b);
   d.snu4 = 0.25 * (1.0 - k.s_nu);
   d.snur4 = 0.25 * k.s_nu * k.rho0;
   d.s3m4 = 0.25 * (1.0 - k.s3);
@@ -102,6 +103,7 @@ inline void fill_f32(DevCoef& k) {
   d.s4m4 = 0.25 * (1.0 - k.s4);
   d.s4r4 = 0.25 * k.s4 * k.rho0;
   d.s4n = k.s4 / 36.0;
+  d.s4r9 = k.s4 * k.rho0 / 36.0;
   d.l1m2 = 0.5 * (1.0 - k.l1);
   d.l1T2 = 0.5 * k.l1 * k.T0;
   d.l2m2 = 0.5 * (1.0 - k.l2);
@@ -110,8 +112,8 @@ inline void fill_f32(DevCoef& k) {
   d.srct2 = 0.5 * k.l2 * k.cT2;
   CollideK<float>& e = k.kf;
   e.hFx = (float)d.hFx;
-  e.hr0 = (float)d.hr0;
-  e.sb4 = (float)d.sb4;
+  e.al = (float)d.al;
+  e.be = (float)d.be;
   e.snu4 = (float)d.snu4;
   e.snur4 = (float)d.snur4;
   e.s3m4 = (float)d.s3m4;
@@ -120,6 +122,7 @@ inline void fill_f32(DevCoef& k) {
   e.s4m4 = (float)d.s4m4;
   e.s4r4 = (float)d.s4r4;
   e.s4n = (float)d.s4n;
+  e.s4r9 = (float)d.s4r9;
   e.l1m2 = (float)d.l1m2;
   e.l1T2 = (float)d.l1T2;
   e.l2m2 = (float)d.l2m2;
