@@ -287,6 +287,15 @@ __host__ __device__ __forceinline__ void fwd1(R am, R a0, R ap, R u, R& c0, R& c
   c1 = s - u * c0;
   c2 = (ap + am) - (u + u) * s + u * u * c0;
 }
+// The same with c0 formed from the pair sum ap + am (one add fewer).
+template <typename R>
+__host__ __device__ __forceinline__ void fwd1q(R am, R a0, R ap, R u, R& c0, R& c1, R& c2) {
+  const R q = ap + am;
+  c0 = q + a0;
+  const R s = ap - am;
+  c1 = s - u * c0;
+  c2 = q - (u + u) * s + u * u * c0;
+}
 // The same from the row's sum c0, difference ap - am and sum ap + am.
 template <typename R>
 __host__ __device__ __forceinline__ void fwd1p(R c0, R s, R q, R u, R& c1, R& c2) {
@@ -368,9 +377,14 @@ __host__ __device__ __forceinline__ void collide(const Co<R>& c, R (&d)[9], R (&
   const R Fy = c.Fvy + c.rgb * dT;
   // Eq. 12 (sum_i w_i e_i = 0, so the rest state adds nothing to j), from the
   // sums and differences of each velocity row, which the x-pass below reuses
-  const R m0 = (d[7] + d[4]) + d[8], ms = d[8] - d[7], mq = d[8] + d[7];  // e_y = -1
-  const R z0 = (d[3] + d[0]) + d[1], zs = d[1] - d[3], zq = d[1] + d[3];  // e_y =  0
-  const R p0 = (d[6] + d[2]) + d[5], ps = d[5] - d[6], pq = d[5] + d[6];  // e_y = +1
+  const R ms = d[8] - d[7], mq = d[8] + d[7];  // e_y = -1
+  const R zs = d[1] - d[3], zq = d[1] + d[3];  // e_y =  0
+  const R ps = d[5] - d[6], pq = d[5] + d[6];  // e_y = +1
+  // row sums: from the pair sums (one add fewer each) where the kernels are
+  // bound by issue, in the grouping the FP32-storage kernels run fastest with otherwise
+  const R m0 = HK ? mq + d[4] : (d[7] + d[4]) + d[8];
+  const R z0 = HK ? zq + d[0] : (d[3] + d[0]) + d[1];
+  const R p0 = HK ? pq + d[2] : (d[6] + d[2]) + d[5];
   const R drho = (m0 + z0) + p0;
   const R rho = c.rho0 + drho;
   const R jx = (ms + zs) + ps;
@@ -393,8 +407,13 @@ __host__ __device__ __forceinline__ void collide(const Co<R>& c, R (&d)[9], R (&
   R b01, b02, b10, b11, b12, b20, b21, b22;
   const R b00 = drho;
   fwd1p(drho, jy, p0 + m0, uy, b01, b02);
-  fwd1(xm1, xz1, xp1, uy, b10, b11, b12);
-  fwd1(xm2, xz2, xp2, uy, b20, b21, b22);
+  if constexpr (HK) {
+    fwd1q(xm1, xz1, xp1, uy, b10, b11, b12);
+    fwd1q(xm2, xz2, xp2, uy, b20, b21, b22);
+  } else {
+    fwd1(xm1, xz1, xp1, uy, b10, b11, b12);
+    fwd1(xm2, xz2, xp2, uy, b20, b21, b22);
+  }
 
   // Eq. 7-10, minus the rest-state moments rho0 kappa_m(ux) kappa_n(uy),
   // kappa = (1, -u, 1/3 + u^2).  Each post-collision moment D_mn is formed
