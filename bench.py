@@ -40,9 +40,9 @@ from paper_1801_04577_gb300 import inputs as I  # noqa: E402
 HBM_FALLBACK_GBS = 6800.0
 # FP64 storage and collision are bound by the FP64 pipe, not by HBM.  FP64 operations per
 # lattice update of step_fused_kernel<double>, counted with ncu on the 2048 x 1024
-# Rayleigh-Benard lattice (sm__sass_thread_inst_executed_op_{dfma,dadd,dmul}_pred_on: 163.8 M
-# DFMA, 163.8 M DADD, 53.6 M DMUL per launch of 2,097,152 nodes; an FMA counts two): 259.9.
-FP64_FLOP_PER_LU = 259.9
+# Rayleigh-Benard lattice (sm__sass_thread_inst_executed_op_{dfma,dadd,dmul}_pred_on: 165.9 M
+# DFMA, 140.7 M DADD, 51.5 M DMUL per launch of 2,097,152 nodes; an FMA counts two): 249.8.
+FP64_FLOP_PER_LU = 249.8
 # FP64 peak of the GB300: 152 SMs x 2 FP64 FMA per clock x 2 flops x 2.07 GHz
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07
 ELEM_BYTES = {"f64": 8, "f32": 4, "f16": 2, "bf16": 2}
@@ -53,11 +53,11 @@ DTYPE = {"f64": "f64", "f32": "f32", "f16": "f16-storage/f32-compute", "bf16": "
 # workload, valid only for the kernel source whose SHA-256 prefix is stored.
 NCU_TRAFFIC = {
     # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum (1 pass) on the full 4096 x 2048
-    # lattice, three launches of step_fused_kernel each: FP32 479.33-479.35 MB read + 414.8-417.7 MB
-    # written; FP16 242.8-243.0 MB read + 185.3-188.2 MB written (the rest of the written lines
+    # lattice, three launches of step_fused_kernel each: FP32 479.30-479.41 MB read + 415.1-418.8 MB
+    # written; FP16 242.8-242.9 MB read + 185.0-187.9 MB written (the rest of the written lines
     # is still dirty in L2 when the launch ends).
-    "f32:rb4096": {"bytes_per_launch": 895.8e6, "kernel_hash": "98d122bd64390927"},
-    "f16:rb4096": {"bytes_per_launch": 429.2e6, "kernel_hash": "98d122bd64390927"},
+    "f32:rb4096": {"bytes_per_launch": 896.2e6, "kernel_hash": "143ac0319ec01428"},
+    "f16:rb4096": {"bytes_per_launch": 429.0e6, "kernel_hash": "143ac0319ec01428"},
 }
 
 
