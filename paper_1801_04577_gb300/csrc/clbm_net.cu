@@ -465,9 +465,14 @@ __global__ void sum_splits_kernel(const float* __restrict__ part, int splits, lo
 }
 
 // launch shape of sum_splits_kernel: R = largest power of two <= min(splits, 32)
-void sum_splits(const float* part, int splits, long long n, float* out, cudaStream_t s) {
+// and <= the rows that keep about one GPU's worth of threads (sms x 2048) busy:
+// many outputs take few rows, each thread then adding more splits in turn (the
+// tree of 32 rows had made the widest sums latency-bound: 51 us for 249 k
+// outputs).
+void sum_splits(const float* part, int splits, long long n, float* out, int sms, cudaStream_t s) {
+  const long long want = std::max<long long>(1, (sms * 2048LL) / std::max<long long>(n, 1));
   int R = 1;
-  while (2 * R <= std::min(splits, kSumRows)) R *= 2;
+  while (2 * R <= std::min(splits, kSumRows) && 2 * R <= want) R *= 2;
   const long long blocks = std::min<long long>((n + 31) / 32, 65535);
   sum_splits_kernel<<<(unsigned)std::max<long long>(blocks, 1), dim3(32, R), 0, s>>>(part, splits, n, out);
 }
@@ -884,12 +889,12 @@ cudaError_t conv_backward(clbm_net* net, const Conv& cv, Act x, Act gy, int gx_i
       gemm_kernel<<<grid, GT, 0, net->stream>>>(la, lb, st, cv.co, Kd, Np, kper);
     }
     const long long n = (long long)cv.co * Kd;
-    sum_splits(net->part, splits, n, net->g + cv.w_off, net->stream);
+    sum_splits(net->part, splits, n, net->g + cv.w_off, net->sms, net->stream);
     // bias: the split-K partials are consumed, so part holds the chunk sums next
     const int chunks = (Np + kBiasChunk - 1) / kBiasChunk;
     if ((long long)chunks * cv.co > net->part_cap) return cudaErrorInvalidValue;
     bias_partial_kernel<<<dim3(chunks, cv.co), GT, 0, net->stream>>>(gy, N, net->part);
-    sum_splits(net->part, chunks, cv.co, net->g + cv.b_off, net->stream);
+    sum_splits(net->part, chunks, cv.co, net->g + cv.b_off, net->sms, net->stream);
   }
   if (gx_id >= 0) {  // input gradient: M = ci, N = pixels, K = co*t, with flipped weights
     const int kk = cv.ks * cv.ks;
