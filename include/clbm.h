@@ -433,14 +433,22 @@ clbm_status clbm_net_param_count(const clbm_net* net, int64_t* count);
 clbm_status clbm_net_get_params(const clbm_net* net, float* dst, int32_t on_device);
 clbm_status clbm_net_set_params(clbm_net* net, const float* src, int32_t on_device);
 
-/* y[N][out_ch][G][G] = net(x[N][in_ch][G][G]), 1 <= N <= max_batch (async). */
+/* y[N][out_ch][G][G] = net(x[N][in_ch][G][G]), 1 <= N <= max_batch (async).
+ * x is copied into the network's input buffer and the output copied to y;
+ * between the copies the forward pass runs as a CUDA graph captured on the
+ * first call with this N (and replayed afterwards), unless the network's
+ * stream cannot be captured (the legacy default stream), where it is
+ * launched kernel by kernel. */
 clbm_status clbm_net_forward(clbm_net* net, const float* x, int32_t n, float* y);
 
 /* Loss and parameter gradients: loss = sum mask (y - t)^2 / (sum mask * out_ch)
  * with mask[N][G][G] (NULL = all ones; the sums are formed on the device, and
  * a mask that sums to zero returns CLBM_EINVAL with the gradients undefined).
  * grad (param_count floats, host or device, may be NULL) receives
- * dloss/dparams; *loss (may be NULL) the loss.  Synchronises once, at the end. */
+ * dloss/dparams; *loss (may be NULL) the loss.  Synchronises once, at the end.
+ * x, target and mask are copied into the network's own buffers first; the
+ * pass (forward, loss, backward) then runs as a CUDA graph captured on the
+ * first call with this N and mask-or-none, as for clbm_net_forward. */
 clbm_status clbm_net_gradients(clbm_net* net, const float* x, const float* target,
                                const float* mask, int32_t n, float* grad, double* loss);
 
