@@ -103,13 +103,18 @@ struct StoreAct {
   int cs, coff, H, W;
   const float* bias;
   int relu, accumulate;
+  // ReLU backward of the accumulated gradient: zero where the forward
+  // activation (same layout as base) is not positive; nullptr = none
+  const float* relu_of = nullptr;
   __device__ __forceinline__ void operator()(int m, int n, float v) const {
     const int hw = H * W;
     const int nb = n / hw, p = n - nb * hw;
-    float* dst = base + ((long long)nb * cs + coff + m) * hw + p;
+    const long long off = ((long long)nb * cs + coff + m) * hw + p;
+    float* dst = base + off;
     if (bias) v += bias[m];
     if (relu) v = v > 0.0f ? v : 0.0f;
     if (accumulate) v += *dst;
+    if (relu_of && !(relu_of[off] > 0.0f)) v = 0.0f;
     *dst = v;
   }
 };
@@ -511,18 +516,6 @@ dim3 plane_grid(int pixels, long long planes) {
   return dim3((unsigned)bx, (unsigned)std::max<long long>(1, std::min<long long>(planes, 65535)));
 }
 
-// g *= (y > 0) over one activation view (ReLU backward, in place on g)
-__global__ void relu_back_kernel(Act y, float* __restrict__ g, int gcs, int gcoff, int N) {
-  const int hw = y.H * y.W;
-  for (int pc = blockIdx.y; pc < N * y.C; pc += gridDim.y) {
-    const int nb = pc / y.C, c = pc - nb * y.C;
-    const float* yp = y.base + ((long long)nb * y.cs + y.coff + c) * hw;
-    float* gp = g + ((long long)nb * gcs + gcoff + c) * hw;
-    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < hw; p += gridDim.x * blockDim.x)
-      if (!(yp[p] > 0.0f)) gp[p] = 0.0f;
-  }
-}
-
 // 2x2 average pool: out (H/2 x W/2) from in; backward adds g_out/4 to the four inputs
 __global__ void pool_kernel(Act in, float* __restrict__ out, int ocs, int ocoff, int N) {
   const int Wo = in.W / 2, ho = (in.H / 2) * Wo, hw = in.H * in.W;
@@ -537,15 +530,21 @@ __global__ void pool_kernel(Act in, float* __restrict__ out, int ocs, int ocoff,
     }
   }
 }
-__global__ void pool_back_kernel(Act gout, float* __restrict__ gin, int gcs, int gcoff, int N) {
+// relu_of (same layout as gin, or nullptr): the ReLU backward of the
+// accumulated gradient, zero where that forward activation is not positive
+__global__ void pool_back_kernel(Act gout, float* __restrict__ gin, int gcs, int gcoff, int N,
+                                 const float* __restrict__ relu_of) {
   const int W = gout.W * 2, hw = gout.H * 2 * W, ho = gout.H * gout.W;
   for (int pc = blockIdx.y; pc < N * gout.C; pc += gridDim.y) {
     const int nb = pc / gout.C, c = pc - nb * gout.C;
     const float* gp = gout.base + ((long long)nb * gout.cs + gout.coff + c) * ho;
-    float* ip = gin + ((long long)nb * gcs + gcoff + c) * hw;
+    const long long base = ((long long)nb * gcs + gcoff + c) * hw;
+    float* ip = gin + base;
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < hw; p += gridDim.x * blockDim.x) {
       const int y = p / W, x = p - y * W;
-      ip[p] += 0.25f * gp[(y >> 1) * gout.W + (x >> 1)];
+      float v = ip[p] + 0.25f * gp[(y >> 1) * gout.W + (x >> 1)];
+      if (relu_of && !(relu_of[base + p] > 0.0f)) v = 0.0f;
+      ip[p] = v;
     }
   }
 }
@@ -563,16 +562,20 @@ __global__ void up_kernel(Act in, float* __restrict__ out, int ocs, int ocoff, i
     }
   }
 }
-__global__ void up_back_kernel(Act gout, float* __restrict__ gin, int gcs, int gcoff, int N) {
+__global__ void up_back_kernel(Act gout, float* __restrict__ gin, int gcs, int gcoff, int N,
+                               const float* __restrict__ relu_of) {
   const int Wi = gout.W / 2, hi = (gout.H / 2) * Wi, hw = gout.H * gout.W;
   for (int pc = blockIdx.y; pc < N * gout.C; pc += gridDim.y) {
     const int nb = pc / gout.C, c = pc - nb * gout.C;
     const float* gp = gout.base + ((long long)nb * gout.cs + gout.coff + c) * hw;
-    float* ip = gin + ((long long)nb * gcs + gcoff + c) * hi;
+    const long long base = ((long long)nb * gcs + gcoff + c) * hi;
+    float* ip = gin + base;
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < hi; p += gridDim.x * blockDim.x) {
       const int y = p / Wi, x = p - y * Wi;
       const float* q = gp + 2 * y * gout.W + 2 * x;
-      ip[p] += (q[0] + q[1]) + (q[gout.W] + q[gout.W + 1]);
+      float v = ip[p] + ((q[0] + q[1]) + (q[gout.W] + q[gout.W + 1]));
+      if (relu_of && !(relu_of[base + p] > 0.0f)) v = 0.0f;
+      ip[p] = v;
     }
   }
 }
@@ -866,8 +869,10 @@ cudaError_t conv_forward(clbm_net* net, const Conv& cv, Act x, int out_id, int o
 
 // Backward of y = act(conv(x)): gy is the gradient buffer of y (ReLU already applied
 // by the caller); accumulates into gx (if gx_id >= 0), writes dW, db.
+// relu_gx: gx is the gradient of a ReLU output whose only contribution is
+// this one, so the ReLU backward is applied in the store (no separate pass).
 cudaError_t conv_backward(clbm_net* net, const Conv& cv, Act x, Act gy, int gx_id, int gx_coff,
-                          int N) {
+                          int N, bool relu_gx = false) {
   const int Kd = cv.ci * cv.ks * cv.ks, Np = N * cv.H * cv.W;
   // weight gradient: M = co, N = ci*t, K = pixels, split-K
   {
@@ -899,6 +904,7 @@ cudaError_t conv_backward(clbm_net* net, const Conv& cv, Act x, Act gy, int gx_i
   if (gx_id >= 0) {  // input gradient: M = ci, N = pixels, K = co*t, with flipped weights
     const int kk = cv.ks * cv.ks;
     StoreAct st{net->gact[gx_id], net->act_c[gx_id], gx_coff, cv.H, cv.W, nullptr, 0, 1};
+    if (relu_gx) st.relu_of = net->act[gx_id];
     if (tensor_math(net)) {  // D(pixel, ci) = sum_k im2col(gy)(pixel, k) W'(ci, k)
       const tc::Packed w = packed_of(net, cv.index, 1);
       const int K = cv.co * kk;
@@ -912,13 +918,6 @@ cudaError_t conv_backward(clbm_net* net, const Conv& cv, Act x, Act gy, int gx_i
     dim3 grid((Np + BN - 1) / BN, (cv.ci + BM - 1) / BM, 1);
     gemm_kernel<<<grid, GT, 0, net->stream>>>(la, lb, st, cv.ci, Np, cv.co * kk, cv.co * kk);
   }
-  return cudaGetLastError();
-}
-
-cudaError_t relu_back(clbm_net* net, int id, int coff, int C, int N) {
-  Act y = view(net, id, coff, C);
-  relu_back_kernel<<<plane_grid(y.H * y.W, (long long)N * C), 256, 0, net->stream>>>(
-      y, net->gact[id], net->act_c[id], coff, N);
   return cudaGetLastError();
 }
 
@@ -967,31 +966,33 @@ cudaError_t backward(clbm_net* net, const Plan& P, int N) {
   {
     const Conv& cv = net->convs[ci--];
     if ((e = conv_backward(net, cv, view(net, P.d2[0], 0, B), view(net, P.out, 0, net->cfg.out_ch, true),
-                           P.d2[0], 0, N))) return e;
+                           P.d2[0], 0, N, true))) return e;
   }
+  // Every ReLU backward is applied where its gradient is complete: in the
+  // input-gradient store of a convolution that is its only source (d2[0], d1,
+  // b1, a1), in the upsampling backward (d2[l > 0], b2) and in the pooling
+  // backward, which adds the last contribution to a skip connection.
   // decoder, shallowest level first (reverse of the forward order)
   for (int l = 0; l <= L - 2; ++l) {
     const int c = B << l, cup = B << (l + 1);
     const Conv& c2 = net->convs[ci--];
     const Conv& c1 = net->convs[ci--];
-    if ((e = relu_back(net, P.d2[l], 0, c, N))) return e;
-    if ((e = conv_backward(net, c2, view(net, P.d1[l], 0, c), view(net, P.d2[l], 0, c, true), P.d1[l], 0, N))) return e;
-    if ((e = relu_back(net, P.d1[l], 0, c, N))) return e;
+    if ((e = conv_backward(net, c2, view(net, P.d1[l], 0, c), view(net, P.d2[l], 0, c, true), P.d1[l], 0, N,
+                           true))) return e;
     if ((e = conv_backward(net, c1, view(net, P.cat[l], 0, cup + c), view(net, P.d1[l], 0, c, true), P.cat[l], 0, N))) return e;
     // gradient of the upsampled part flows to the level below (d2[l+1] or b2)
     const int below = (l + 1 <= L - 2) ? P.d2[l + 1] : P.b2;
     Act gup = view(net, P.cat[l], 0, cup, true);
     up_back_kernel<<<plane_grid((gup.H / 2) * (gup.W / 2), (long long)N * cup), 256, 0, net->stream>>>(
-        gup, net->gact[below], net->act_c[below], 0, N);
+        gup, net->gact[below], net->act_c[below], 0, N, net->act[below]);
   }
   // bottleneck
   {
     const int cb = B << (L - 1);
     const Conv& c2 = net->convs[ci--];
     const Conv& c1 = net->convs[ci--];
-    if ((e = relu_back(net, P.b2, 0, cb, N))) return e;
-    if ((e = conv_backward(net, c2, view(net, P.b1, 0, cb), view(net, P.b2, 0, cb, true), P.b1, 0, N))) return e;
-    if ((e = relu_back(net, P.b1, 0, cb, N))) return e;
+    if ((e = conv_backward(net, c2, view(net, P.b1, 0, cb), view(net, P.b2, 0, cb, true), P.b1, 0, N,
+                           true))) return e;
     const int inb = P.pool[L - 2];
     if ((e = conv_backward(net, c1, view(net, inb, 0, B << (L - 2)), view(net, P.b1, 0, cb, true),
                            inb, 0, N))) return e;
@@ -1004,10 +1005,9 @@ cudaError_t backward(clbm_net* net, const Plan& P, int N) {
     // pool backward adds into the skip part of cat[l]
     Act gp = view(net, P.pool[l], 0, c, true);
     pool_back_kernel<<<plane_grid(gp.H * 2 * gp.W * 2, (long long)N * c), 256, 0, net->stream>>>(
-        gp, net->gact[P.cat[l]], net->act_c[P.cat[l]], cup, N);
-    if ((e = relu_back(net, P.cat[l], cup, c, N))) return e;
-    if ((e = conv_backward(net, c2, view(net, P.a1[l], 0, c), view(net, P.cat[l], cup, c, true), P.a1[l], 0, N))) return e;
-    if ((e = relu_back(net, P.a1[l], 0, c, N))) return e;
+        gp, net->gact[P.cat[l]], net->act_c[P.cat[l]], cup, N, net->act[P.cat[l]]);
+    if ((e = conv_backward(net, c2, view(net, P.a1[l], 0, c), view(net, P.cat[l], cup, c, true), P.a1[l], 0, N,
+                           true))) return e;
     const int inb = l > 0 ? P.pool[l - 1] : P.in;
     const int cin = l > 0 ? (B << (l - 1)) : net->cfg.in_ch;
     if ((e = conv_backward(net, c1, view(net, inb, 0, cin), view(net, P.a1[l], 0, c, true),
