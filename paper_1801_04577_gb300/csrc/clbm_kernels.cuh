@@ -997,9 +997,16 @@ __global__ void __launch_bounds__(kRedThreads) boundary_kernel(const StepArgs a)
 // interior tiles of rows that are not boundary rows, which skip the first and
 // last column.  The latency-bound boundary work then overlaps the streaming
 // interior work instead of following it.
+// Blocks per SM the register budget is cut for: five (96 registers) where the
+// step is memory-bound (FP32, FP64 storage); six (80 registers, a 44-byte
+// spill) for 16-bit storage, which is bound by issue and memory latency and
+// gains 2-6 % from the extra warps (measured A/B on one GB300).
+template <typename S>
+constexpr int kStepBlocks = sizeof(S) == 2 ? 6 : 5;
+
 template <typename S, bool VH, bool MASKED = false>
-__global__ void __launch_bounds__(kStepThreads, 5) step_fused_kernel(const StepArgs a, int nbb,
-                                                                  int xblocks, int y0, int rows) {
+__global__ void __launch_bounds__(kStepThreads, kStepBlocks<S>) step_fused_kernel(const StepArgs a, int nbb,
+                                                                                int xblocks, int y0, int rows) {
   using R = typename Traits<S>::R;
   constexpr int V = Traits<S>::V;
   const Co<R> c = make_co<R>(a.c);
