@@ -1,7 +1,8 @@
 // Test harness: the library's single-node collision (clbm::collide, the code
-// every step kernel inlines) compiled for the host, so that CPU tests can set
-// it against the FP64 oracle's collision node by node.  Not part of the
-// library; built by tests/test_collide_host.py.
+// every step kernel inlines) and its equilibrium (clbm::equilibrium, the
+// initialisation) compiled for the host, so that CPU tests can set them
+// against the FP64 oracle node by node.  Not part of the library; built by
+// tests/test_collide_host.py.
 #include "../paper_1801_04577_gb300/csrc/clbm_kernels.cuh"
 
 namespace {
@@ -57,5 +58,18 @@ extern "C" int host_collide(const double* rates, int vh, int form, double* d, do
     run<float, false>(k, vh, d, h, qv);
   else
     return 1;
+  return 0;
+}
+
+// d[9], h[5] out: equilibrium deviations from the rest state at (rho, ux, uy,
+// T), in FP64.
+extern "C" int host_equilibrium(const double* rates, double rho, double ux, double uy, double T, double* d,
+                                double* h) {
+  const clbm::DevCoef k = coef_of(rates, 0);
+  const clbm::Co<double> c = clbm::make_co<double>(k);
+  double dd[9], hh[5];
+  clbm::equilibrium(c, rho, ux, uy, T, dd, hh);
+  for (int i = 0; i < 9; ++i) d[i] = dd[i];
+  for (int i = 0; i < 5; ++i) h[i] = hh[i];
   return 0;
 }

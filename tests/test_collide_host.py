@@ -43,6 +43,8 @@ def harness(tmp_path_factory):
     dp = C.POINTER(C.c_double)
     L.host_collide.argtypes = [dp, C.c_int, C.c_int, dp, dp, dp]
     L.host_collide.restype = C.c_int
+    L.host_equilibrium.argtypes = [dp, C.c_double, C.c_double, C.c_double, C.c_double, dp, dp]
+    L.host_equilibrium.restype = C.c_int
     return L
 
 
@@ -118,3 +120,22 @@ def test_harness_detects_a_mis_scaled_rate(harness):
     qv = np.zeros(1)
     harness.host_collide(_dp(bad), 0, 0, _dp(d), _dp(h), _dp(qv))
     assert np.abs(d + f_rest - fs).max() > 1e-6
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_host_equilibrium_matches_oracle(harness, name):
+    """The initialisation's equilibrium (Eq. 9 and Eq. 19 through the
+    tensor-product inverse transforms, as deviations from the rest state)
+    against the oracle's, which inverts the paper's matrices."""
+    p, o, rates, f_rest, g_rest = _setup(name)
+    r = I.splitmix64_uniform(31, 64 * 4).reshape(64, 4)
+    worst = 0.0
+    for a in r:
+        rho = p.rho0 * (1 + 0.05 * (2 * a[0] - 1))
+        ux, uy = 0.1 * (2 * a[1] - 1), 0.1 * (2 * a[2] - 1)
+        T = p.T0 + 0.5 * (2 * a[3] - 1)
+        f, g = o.equilibrium(rho, ux, uy, T)
+        d, h = np.zeros(9), np.zeros(5)
+        assert harness.host_equilibrium(_dp(rates), rho, ux, uy, T, _dp(d), _dp(h)) == 0
+        worst = max(worst, np.abs(d + f_rest - f).max(), np.abs(h + g_rest - g).max())
+    assert worst <= 2e-15, (name, worst)
