@@ -73,3 +73,19 @@ extern "C" int host_equilibrium(const double* rates, double rho, double ux, doub
   for (int i = 0; i < 5; ++i) h[i] = hh[i];
   return 0;
 }
+
+// The wall rules of the fix-up (Eq. 28 and its off-midpoint form): which = 0
+// wall_temperature, 1 wall_temperature_q, 2 midpoint_temperature_q; a[] holds
+// the arguments in the functions' order; f32 != 0 evaluates in FP32.
+extern "C" double host_wall(int which, int f32, const double* a) {
+  if (f32) {
+    float v[9];
+    for (int i = 0; i < 9; ++i) v[i] = (float)a[i];
+    if (which == 0) return clbm::wall_temperature(v[0], v[1], v[2], v[3], v[4], v[5], a[6] != 0);
+    if (which == 1) return clbm::wall_temperature_q(v[0], v[1], v[2], v[3], v[4], v[5], v[6], a[7] != 0);
+    return clbm::midpoint_temperature_q(v[0], v[1], v[2], v[3], a[4] != 0, v[5], a[6] != 0, a[7] != 0);
+  }
+  if (which == 0) return clbm::wall_temperature(a[0], a[1], a[2], a[3], a[4], a[5], a[6] != 0);
+  if (which == 1) return clbm::wall_temperature_q(a[0], a[1], a[2], a[3], a[4], a[5], a[6], a[7] != 0);
+  return clbm::midpoint_temperature_q(a[0], a[1], a[2], a[3], a[4] != 0, a[5], a[6] != 0, a[7] != 0);
+}

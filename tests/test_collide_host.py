@@ -45,6 +45,8 @@ def harness(tmp_path_factory):
     L.host_collide.restype = C.c_int
     L.host_equilibrium.argtypes = [dp, C.c_double, C.c_double, C.c_double, C.c_double, dp, dp]
     L.host_equilibrium.restype = C.c_int
+    L.host_wall.argtypes = [C.c_int, C.c_int, dp]
+    L.host_wall.restype = C.c_double
     return L
 
 
@@ -139,3 +141,37 @@ def test_host_equilibrium_matches_oracle(harness, name):
         assert harness.host_equilibrium(_dp(rates), rho, ux, uy, T, _dp(d), _dp(h)) == 0
         worst = max(worst, np.abs(d + f_rest - f).max(), np.abs(h + g_rest - g).max())
     assert worst <= 2e-15, (name, worst)
+
+
+@pytest.mark.parametrize("f32,tol", [(0, 4e-15), (1, 2e-6)])
+def test_host_wall_rules_match_oracle(harness, f32, tol):
+    """The fix-up's wall temperature (Eq. 28, one- and two-point), its form for
+    walls off the link midpoint, and the midpoint value Eq. 26 imposes there,
+    against the oracle's own implementations, on random conditions (Dirichlet,
+    Neumann, Robin), link fractions and temperatures; relative to the scale of
+    the temperatures involved (measured 3.3e-16 in FP64, 3.2e-7 in FP32)."""
+    r = I.splitmix64_uniform(57, 400 * 8).reshape(400, 8)
+    worst = 0.0
+    for k, a in enumerate(r):
+        kind = k % 3  # Dirichlet (b1 = 0), Neumann (b2 = 0), Robin
+        b1 = 0.0 if kind == 0 else 0.5 + a[0]
+        b2 = 0.0 if kind == 1 else 0.5 + a[1]
+        b3 = 2 * a[2] - 1
+        ne = [1.0, 0.7071067811865476, 0.55][k % 3]
+        q = 0.05 + 0.95 * a[3]
+        T1, T2, T3 = 2 * a[4] - 1, 2 * a[5] - 1, 2 * a[6] - 1
+        have2 = a[7] > 0.2
+        have3 = a[7] > 0.4
+        scale = 1 + abs(b3) / max(b2, 1e-3) + abs(T1) + abs(T2) + abs(T3)
+        got = harness.host_wall(0, f32, _dp(np.array([b1, b2, b3, ne, T1, T2, float(have2), 0, 0])))
+        want = oracle.wall_temperature(b1, b2, b3, ne, T1, T2, have2)
+        worst = max(worst, abs(got - want) / scale)
+        got = harness.host_wall(1, f32, _dp(np.array([b1, b2, b3, ne, q, T1, T2, float(have2), 0])))
+        want = oracle.wall_temperature_q(b1, b2, b3, ne, q, T1, T2, have2)
+        worst = max(worst, abs(got - want) / scale)
+        Tw = want
+        got = harness.host_wall(2, f32, _dp(np.array([q, Tw, T1, T2, float(have2), T3, float(have3),
+                                                      float(kind == 0), 0])))
+        want = oracle.midpoint_temperature_q(q, Tw, T1, T2, T3, have2, have3, kind == 0)
+        worst = max(worst, abs(got - want) / (scale + abs(Tw)))
+    assert worst <= tol, worst
